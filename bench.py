@@ -1,0 +1,380 @@
+"""Benchmark of the GB300 trajectory distance threshold search.
+
+Workload (default): the Random-walk 1M configuration -- 2,500 random-walk trajectories x 401
+samples (1,000,000 database segments), 25 query trajectories (10,000 query segments), full time
+span, d in {1, 5, 10, 25}. One step = one query batch searched at every d with every index
+(spatiotemporal, temporal, spatial when available): the whole search path (query preparation,
+schedule, grouping, pair kernel count pass, scan, write pass) per search, inputs resident in HBM.
+
+Prints ONE JSON line (rank 0). With --impl reference the CPU oracle is timed instead on the host
+cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "seg-pair tests/s & query segs/s, plain vs batched/served; p50/p99 latency"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+FP64_PEAK_TFLOPS = 1.25                              # GB300 FP64 (nominal)
+PREFILTER_FLOPS = 20       # FP32 flops per candidate test (6 sub, 6 max, 1 mul + 2 fma, 3 cmp)
+EXACT_FLOPS = 41           # FP64 flops per exact test (window, positions, a, b, c, decision)
+INTERVAL_FLOPS = 10        # FP64 flops per hit for the roots (sqrt, 2 div, clamps)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="random-walk-1m")
+    ap.add_argument("--indexes", default="spatiotemporal,temporal")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_workload(name, rank):
+    from paper_1410_2698_gb300 import workloads
+    if name == "random-walk-1m":
+        w = workloads.random_walk_1m()
+        if rank:
+            # each rank searches its own query batch (weak scaling): other query trajectories
+            qrng = np.random.Generator(np.random.PCG64(workloads.SEED_BASE + 1 + 1000 + rank))
+            q_traj = np.sort(qrng.choice(2500, size=25, replace=False))
+            w.queries = workloads._query_from_traj(w.db, 400, q_traj)
+        return w
+    if name == "tiny":
+        return workloads.tiny()
+    if name == "dense":
+        return workloads.dense()
+    if name == "merger-like":
+        return workloads.merger_like()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                mx.append(float(f[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline(tot, pair_ms):
+    """Roofline of the pair kernel (count + write passes): the slower of the FP32 filter and the
+    FP64 exact test at their pipes' peaks; algorithmic work counted once."""
+    t_s = pair_ms / 1e3
+    f32 = tot["n_tests"] * PREFILTER_FLOPS
+    f64 = tot["n_exact"] * EXACT_FLOPS + tot["n_hits"] * INTERVAL_FLOPS
+    lb32 = f32 / (FP32_PEAK_TFLOPS * 1e12)
+    lb64 = f64 / (FP64_PEAK_TFLOPS * 1e12)
+    if lb32 >= lb64:
+        ach = f32 / t_s / 1e12 if t_s > 0 else 0.0
+        peak = FP32_PEAK_TFLOPS
+        pipe = "fp32 (conservative filter)"
+    else:
+        ach = f64 / t_s / 1e12 if t_s > 0 else 0.0
+        peak = FP64_PEAK_TFLOPS
+        pipe = "fp64 (exact test)"
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak if peak else None, "traffic": None,
+            "kernel": "k_pair (count + write passes)", "pipe": pipe,
+            "peak_source": "derived: 152 SMs x lanes x 2.07 GHz (FP32), GB300 nominal (FP64)"}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1410_2698_gb300 import api
+    from paper_1410_2698_gb300.workloads import Segments
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = load_workload(args.workload, rank)
+    kinds = [k for k in args.indexes.split(",") if k]
+    indexes = {k: api.ts_build_index(w.db, kind=k) for k in kinds}
+    qdev = {f: torch.from_numpy(getattr(w.queries, f)).to(dev) for f in Segments.FIELDS}
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+    stream = torch.cuda.current_stream()
+
+    def one_step(collect=None):
+        for k in kinds:
+            for d in w.distances:
+                r = api.ts_search(indexes[k], qdev, d, w.t_start, w.t_end)
+                if collect is not None:
+                    collect.append((k, d, r.stats))
+                r.free()
+
+    for _ in range(max(args.warmup, 0)):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = api.ts_kernel_launches()
+    step_ms = []
+    per = []
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed events
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        one_step(per)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    launches = api.ts_kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    tot = {k: 0 for k in ("n_tests", "n_exact", "n_hits", "n_qsegs")}
+    pair_ms = 0.0
+    breakdown = {}
+    for k, d, st in per:
+        for key in tot:
+            tot[key] += st[key]
+        pair_ms += st["ms_count_pass"] + st["ms_write_pass"]
+        b = breakdown.setdefault(f"{k}@d={d:g}", {"tests": 0, "hits": 0, "pair_ms": 0.0,
+                                                  "exact": 0, "subbin_queries": 0})
+        b["tests"] += st["n_tests"]
+        b["hits"] += st["n_hits"]
+        b["exact"] += st["n_exact"]
+        b["subbin_queries"] += st["n_subbin"]
+        b["pair_ms"] += st["ms_count_pass"] + st["ms_write_pass"]
+    for b in breakdown.values():
+        for key in ("tests", "hits", "exact", "subbin_queries"):
+            b[key] //= max(args.steps, 1)
+        b["pair_ms"] /= max(args.steps, 1)
+    # whole-job aggregates (all ranks process the same amount of work)
+    qsegs_job = tot["n_qsegs"] * world
+    tests_job = tot["n_tests"] * world
+    value = qsegs_job / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "query segs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded random walks; stand-in for the paper's Random-1M)",
+        "config": {"workload": f"{w.name}: {w.db.n} db segments, {w.queries.n} query segments, "
+                               f"d in {list(w.distances)}, indexes {kinds}, plain per-query-batch "
+                               "search (one ts_search per index and d)",
+                   "l2": "flushed (256 MB write) between timed steps", "form": "plain"},
+        "tests_per_s": tests_job / (total_ms / 1e3),
+        "hits_per_step": tot["n_hits"] // max(args.steps, 1),
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": roofline(tot, pair_ms),
+        "pair_kernel_share": pair_ms / total_ms if total_ms else None,
+        "breakdown": breakdown,
+    }
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(args, api, w, indexes, kinds)
+    if world > 1:
+        dist.barrier()
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w)
+    for idx in indexes.values():
+        idx.free()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, api, w, indexes, kinds):
+    """The same step through the C ABI with HOST buffers: H2D of the queries and D2H of every
+    result row inside the timed region."""
+    import torch
+    stream = torch.cuda.current_stream()
+    h2d = 0
+    d2h = 0
+    ms = []
+    for s in range(args.steps + 1):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h2d_s = d2h_s = 0
+        qsegs = 0
+        for k in kinds:
+            for d in w.distances:
+                r = api.ts_search(indexes[k], w.queries, d, w.t_start, w.t_end)
+                rows = r.to_host()
+                h2d_s += 8 * 8 * w.queries.n
+                d2h_s += rows["q_idx"].nbytes * 2 + rows["t_in"].nbytes * 2
+                qsegs += r.stats["n_qsegs"]
+                r.free()
+        b.record(stream)
+        b.synchronize()
+        if s > 0:  # first pass is warm-up
+            ms.append(a.elapsed_time(b))
+            h2d, d2h = h2d_s, d2h_s
+    t = sum(ms) / 1e3
+    return {"value": qsegs * len(ms) / t, "unit": "query segs/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def cpu_baseline(w, budget_s=8.0):
+    """The oracle as it stands, on all host cores (OpenMP), on a bounded sample of the
+    workload's query segments at every d; reported in query segs/s."""
+    import oracle
+    from paper_1410_2698_gb300.workloads import Segments
+    threads = os.cpu_count() or 1
+    nq = w.queries.n
+    take = min(nq, 500)
+    spent = 0.0
+    qsegs = 0
+    tests = 0
+    rounds = 0
+    while spent < budget_s and take <= nq:
+        sub = w.queries.take(np.arange(take))
+        t0 = time.perf_counter()
+        for d in w.distances:
+            _, nt, nqs = oracle.search_count(w.db, sub, w.t_start, w.t_end, d, threads=threads)
+            qsegs += nqs
+            tests += nt
+        spent += time.perf_counter() - t0
+        rounds += 1
+        if take == nq:
+            break
+        take = min(nq, take * 2)
+    return {"value": qsegs / spent, "unit": "query segs/s", "cores": threads, "kind": "oracle",
+            "tests_per_s": tests / spent,
+            "sample": f"{rounds} passes over the first up-to-{take} query segments x "
+                      f"{len(w.distances)} distances ({spent:.1f} s of CPU time)"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    w = load_workload(args.workload, 0)
+    threads = os.cpu_count() or 1
+    sample = w.queries.take(np.arange(min(w.queries.n, 800)))
+    for _ in range(max(args.warmup, 0)):
+        oracle.search_count(w.db, sample.take(np.arange(50)), w.t_start, w.t_end, w.distances[0],
+                            threads=threads)
+    total = 0.0
+    qsegs = 0
+    tests = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for d in w.distances:
+            _, nt, nq = oracle.search_count(w.db, sample, w.t_start, w.t_end, d, threads=threads)
+            qsegs += nq
+            tests += nt
+        total += time.perf_counter() - t0
+    value = qsegs / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "query segs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.db.n} db segments, sample of {sample.n} of "
+                                   f"{w.queries.n} query segments, d in {list(w.distances)}"},
+            "cpu_baseline": {"value": value, "unit": "query segs/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": f"{sample.n} query segments x {len(w.distances)} d per step"},
+            "e2e": {"value": value, "unit": "query segs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "tests_per_s": tests / total}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * ts.h -- C ABI of libts_gb300, a GB300 (sm_103a) distance threshold search over historical
+ * continuous trajectories, after Gowanlock & Casanova, "Towards Efficient Indexing of
+ * Spatiotemporal Trajectories on the GPU for Distance Threshold Similarity Searches".
+ *
+ * Problem (Sec. 3.1): a database D of 4-D line segments (x, y, z, t start point to end point;
+ * linear motion in between) and a set Q of query segments. For a distance d and a query interval
+ * [t_start, t_end] the search returns every (q, l) pair whose common time window, clipped to the
+ * interval, has positive length and contains instants at which the two moving points are within
+ * d of each other, together with the sub-interval [t_in, t_out] of those instants (a convex
+ * quadratic's non-positive set, so one interval per pair).
+ *
+ * D and its index are built once and stay resident on the GPU; they are queried many times
+ * (Sec. 3.1, platform). Three indexes prune the candidates (Sec. 4.1 spatial grid, Sec. 4.2
+ * temporal bins, Sec. 4.3 spatiotemporal subbins); all return the same pair set as the plain
+ * all-pairs search (TS_INDEX_BRUTE).
+ *
+ * Conventions of every call:
+ *  - Status codes: every call returns ts_status; nothing throws across this boundary. On error a
+ *    thread-local message is available from ts_last_error().
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Work
+ *    is stream ordered.
+ *  - Pointers: ts_segments arrays are device pointers unless on_host = 1; they stay owned by the
+ *    caller and are only read.
+ *  - Precision: coordinates, times, d and result times are IEEE FP64.
+ *  - Handles: ts_index and ts_result are opaque, owned by the library and released with
+ *    ts_free(). An index is immutable after ts_build_index() returns and can be searched from
+ *    several host threads and streams at once.
+ *  - Determinism: for a given index, query set and parameters the rows, their order and every
+ *    bit of t_in / t_out are the same from run to run.
+ */
+#ifndef TS_GB300_H
+#define TS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ts_status {
+    TS_OK = 0,
+    TS_ERR_INVALID_ARG = 1, /* bad argument or input value (NaN/Inf, t_end <= t_start, d <= 0) */
+    TS_ERR_OOM = 2,         /* device or host allocation failed */
+    TS_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error string) */
+    TS_ERR_CAPACITY = 4,    /* result count above the caller's max_results (count still given) */
+    TS_ERR_TIMEOUT = 5,     /* a bounded device-side or host-side wait ran out */
+    TS_ERR_CANCELLED = 6,   /* the request was cancelled (server) */
+    TS_ERR_INTERNAL = 7     /* an internal consistency check failed */
+} ts_status;
+
+typedef enum ts_index_kind {
+    TS_INDEX_BRUTE = 0,          /* no pruning: every query against every entry (reference mode) */
+    TS_INDEX_SPATIAL = 1,        /* flatly structured grid, Sec. 4.1 (GPUSpatial) */
+    TS_INDEX_TEMPORAL = 2,       /* temporal bins, Sec. 4.2 (GPUTemporal) */
+    TS_INDEX_SPATIOTEMPORAL = 3  /* temporal bins split into spatial subbins, Sec. 4.3 */
+} ts_index_kind;
+
+/* A set of line segments in structure-of-arrays FP64 form (Sec. 3.1): segment i goes from
+ * (x0[i], y0[i], z0[i]) at time t0[i] to (x1[i], y1[i], z1[i]) at time t1[i], t1[i] > t0[i]. */
+typedef struct ts_segments {
+    const double *x0, *y0, *z0, *t0;
+    const double *x1, *y1, *z1, *t1;
+    uint64_t n;       /* number of segments; at most 2^31 - 1 */
+    int32_t on_host;  /* 0: device pointers; 1: host pointers, copied to the device by the call */
+    int32_t reserved;
+} ts_segments;
+
+/* Index parameters; 0 selects the library's default for that field. */
+typedef struct ts_index_params {
+    int32_t kind;        /* ts_index_kind */
+    uint32_t t_bins;     /* m: temporal bins (Sec. 4.2); used by TEMPORAL and SPATIOTEMPORAL */
+    uint32_t sub_bins;   /* v: subbins per dimension (Sec. 4.3), lowered per dimension so that a
+                            subbin is at least as wide as the longest entry in that dimension */
+    uint32_t grid_cells; /* cells per dimension of the spatial grid (Sec. 4.1), at most 512 */
+} ts_index_params;
+
+/* Search parameters. */
+typedef struct ts_query_params {
+    double d;            /* distance threshold, finite and > 0 */
+    double t_start;      /* query interval [t_start, t_end] (Sec. 1); t_start <= t_end */
+    double t_end;
+    uint64_t max_results; /* 0 = unlimited; else more rows -> TS_ERR_CAPACITY (paper's result
+                             buffer and incremental processing, Sec. 5.2) */
+} ts_query_params;
+
+/* Counters of one search (all exact, counted on the device). */
+typedef struct ts_search_stats {
+    uint64_t n_queries;   /* query segments passed in */
+    uint64_t n_qsegs;     /* query segments with a positive-length overlap with [t_start, t_end] */
+    uint64_t n_tests;     /* candidate (query, entry) pairs the index produced and the pair
+                             kernel evaluated */
+    uint64_t n_exact;     /* candidates that passed the conservative FP32 filter and were
+                             decided by the FP64 test */
+    uint64_t n_hits;      /* result rows */
+    uint64_t n_tiles;     /* work tiles (query group x candidate range) */
+    uint64_t n_groups;    /* query groups (up to 32 queries sharing a candidate range) */
+    uint64_t n_subbin;    /* queries served from a subbin range (spatiotemporal index) */
+    double ms_count_pass; /* device time of the pair kernel's count pass (CUDA events) */
+    double ms_write_pass; /* device time of the pair kernel's write pass (CUDA events) */
+} ts_search_stats;
+
+/* Read-only description of a built index. */
+typedef struct ts_index_info {
+    int32_t kind;
+    uint32_t t_bins;        /* m actually used */
+    uint32_t sub_bins[3];   /* v actually used per dimension (x, y, z) */
+    uint32_t grid_cells;    /* cells per dimension actually used */
+    uint64_t n;             /* entry segments */
+    uint64_t st_len[3];     /* length of the X, Y, Z id arrays (Sec. 4.3) */
+    uint64_t grid_len;      /* length of the grid lookup array A (Sec. 4.1) */
+    uint64_t device_bytes;  /* device memory held by the index */
+    double t_min, t_max, bin_width;
+    double sub_lo[3], sub_w[3];
+    double grid_lo[3], grid_w[3];
+} ts_index_info;
+
+typedef struct ts_index ts_index;
+typedef struct ts_result ts_result;
+
+/*
+ * Build the index of database `db` (Sec. 4.1-4.3). The database is validated (finite values,
+ * t1 > t0; else TS_ERR_INVALID_ARG), sorted by start time (Sec. 4.2), given velocities, and
+ * binned; the segments are copied, so the caller may release db's arrays once the call returns.
+ * The call synchronises `stream` (index building is offline work, Sec. 5.2). On success *out
+ * owns the index (release with ts_free).
+ */
+ts_status ts_build_index(const ts_segments *db, const ts_index_params *params, void *stream,
+                         ts_index **out);
+
+/* Describe a built index. */
+ts_status ts_index_get_info(const ts_index *idx, ts_index_info *info);
+
+/* Fields exported by ts_index_export (for inspection and tests). `dim` selects x/y/z where noted. */
+typedef enum ts_index_field {
+    TS_FIELD_PERM = 0,       /* uint32[n]: sorted position -> caller's entry index (Sec. 4.2) */
+    TS_FIELD_BIN_START = 1,  /* double[m]: B_j^start */
+    TS_FIELD_BIN_END = 2,    /* double[m]: B_j^end */
+    TS_FIELD_BIN_OFF = 3,    /* uint32[m+1]: first entry of bin j (B_j^first), last = next - 1 */
+    TS_FIELD_ST_IDS = 4,     /* uint32[st_len[dim]]: X, Y or Z id array (sorted positions) */
+    TS_FIELD_ST_OFF = 5,     /* uint32[v*m+1]: subbin (i, j) range starts at off[j*m + i] */
+    TS_FIELD_GRID_A = 6,     /* uint32[grid_len]: lookup array A (sorted positions) */
+    TS_FIELD_GRID_OFF = 7    /* uint32[g^3+1]: cell h range starts at off[h] */
+} ts_index_field;
+
+/* Copy one internal array of the index to host memory `dst` of `capacity` bytes. *size receives
+ * the array's byte size; TS_ERR_CAPACITY (nothing copied) when capacity is too small. */
+ts_status ts_index_export(const ts_index *idx, int32_t field, int32_t dim, void *dst,
+                          uint64_t capacity, uint64_t *size);
+
+/*
+ * Per-query candidate schedule (Sec. 4.2 schedule S, Sec. 4.3 schedule with array selector):
+ * for every query segment, in the caller's order, sel = 0/1/2 for a range of the X/Y/Z id array,
+ * 3 for a range of the time-sorted entries; [lo, hi) is the half-open range. Queries whose
+ * clipped window is empty get sel = 3, lo = hi = 0. For TS_INDEX_BRUTE the range is [0, n); for
+ * TS_INDEX_SPATIAL, sel = 4 and lo/hi hold the number of raw and duplicate-free candidates.
+ * sel, lo, hi are host arrays of q->n elements. Synchronises `stream`.
+ */
+ts_status ts_schedule(const ts_index *idx, const ts_segments *q, const ts_query_params *qp,
+                      void *stream, int32_t *sel, uint64_t *lo, uint64_t *hi);
+
+/*
+ * Search the index with the query segments `q` (Alg. 1-3 of the paper, re-designed: count pass,
+ * exclusive scan, write pass, so the output is exact-size and deterministic). Rows are grouped by
+ * work tile in a fixed tile order; sort by (q_idx, e_idx) for a canonical order. q_idx is the
+ * caller's query index, e_idx the caller's database index. The call synchronises `stream` once
+ * (to size the result). On TS_ERR_CAPACITY *out still receives a result whose count is the exact
+ * number of rows and whose row arrays are empty, so the caller can split Q and retry.
+ */
+ts_status ts_search(const ts_index *idx, const ts_segments *q, const ts_query_params *qp,
+                    void *stream, ts_result **out);
+
+/* Number of rows of a result. */
+uint64_t ts_result_count(const ts_result *r);
+
+/* Device pointers to the result rows (structure of arrays, ts_result_count elements each, owned
+ * by the result). NULL pointers are allowed for fields the caller does not need. */
+ts_status ts_result_arrays(const ts_result *r, const uint32_t **q_idx, const uint32_t **e_idx,
+                           const double **t_in, const double **t_out);
+
+/* Counters of the search that produced `r`. */
+ts_status ts_result_stats(const ts_result *r, ts_search_stats *stats);
+
+/* Copy the rows to host arrays of at least ts_result_count elements (NULL = skip the field).
+ * Synchronises `stream`. */
+ts_status ts_result_copy_to_host(const ts_result *r, uint32_t *q_idx, uint32_t *e_idx,
+                                 double *t_in, double *t_out, void *stream);
+
+/* Release a ts_index or ts_result (NULL is a no-op). Waits for the device work of the handle. */
+void ts_free(void *handle);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *ts_last_error(void);
+
+/* Number of kernels this library has launched in this process so far (all streams, all
+ * devices); the difference across a region counts the launches inside it. */
+uint64_t ts_kernel_launches(void);
+
+/* Library version string. */
+const char *ts_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TS_GB300_H */

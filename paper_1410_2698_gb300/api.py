@@ -1,0 +1,250 @@
+"""Python binding of the C ABI (include/ts.h): same names, argument marshalling only.
+
+Segment sets may be given as a ``workloads.Segments`` of numpy arrays (host memory: the library
+copies them to the device inside the call) or as any object whose eight fields x0, y0, z0, t0,
+x1, y1, z1, t1 are contiguous float64 CUDA tensors (device memory, read in place). Every step of
+the search runs in the CUDA library; nothing here computes.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import TsError, check
+
+FIELDS8 = ("x0", "y0", "z0", "t0", "x1", "y1", "z1", "t1")
+
+
+def _current_stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:  # pragma: no cover
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _columns(segs):
+    if isinstance(segs, dict):
+        return [segs[f] for f in FIELDS8]
+    if isinstance(segs, (list, tuple)) and len(segs) == 8:
+        return list(segs)
+    return [getattr(segs, f) for f in FIELDS8]
+
+
+def make_segments(segs):
+    """Marshal a segment set into a ts_segments struct. Returns (struct, keepalive)."""
+    cols = _columns(segs)
+    first = cols[0]
+    s = _lib.ts_segments()
+    keep = []
+    if isinstance(first, np.ndarray):
+        arrs = [np.ascontiguousarray(c, dtype=np.float64) for c in cols]
+        n = arrs[0].shape[0]
+        for name, a in zip(FIELDS8, arrs):
+            if a.shape != (n,):
+                raise ValueError("all eight columns must be 1-D of equal length")
+            setattr(s, name, a.ctypes.data if n else None)
+        s.n = n
+        s.on_host = 1
+        keep = arrs
+    else:  # torch tensors on the GPU
+        import torch
+        n = int(first.shape[0])
+        for name, t in zip(FIELDS8, cols):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                    and t.is_contiguous() and t.dim() == 1 and int(t.shape[0]) == n):
+                raise ValueError("device columns must be contiguous 1-D float64 CUDA tensors")
+            setattr(s, name, t.data_ptr() if n else None)
+        s.n = n
+        s.on_host = 0
+        keep = cols
+    return s, keep
+
+
+class Index:
+    """Owner of a ts_index handle."""
+
+    def __init__(self, handle, n):
+        self._h = handle
+        self.n = n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        return ts_index_get_info(self)
+
+    def free(self):
+        if self._h:
+            _lib.load().ts_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Result:
+    """Owner of a ts_result handle."""
+
+    def __init__(self, handle, status):
+        self._h = handle
+        self.status = status
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def count(self) -> int:
+        return int(_lib.load().ts_result_count(self._h))
+
+    @property
+    def stats(self) -> dict:
+        return ts_result_stats(self)
+
+    def to_host(self, stream=None, sort=False):
+        return ts_result_copy_to_host(self, stream=stream, sort=sort)
+
+    def device_arrays(self):
+        return ts_result_arrays(self)
+
+    def free(self):
+        if self._h:
+            _lib.load().ts_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def ts_version() -> str:
+    return _lib.load().ts_version().decode()
+
+
+def ts_build_index(db, kind="temporal", t_bins=0, sub_bins=0, grid_cells=0, stream=None) -> Index:
+    lib = _lib.load()
+    s, keep = make_segments(db)
+    p = _lib.ts_index_params(_lib.KINDS[kind] if isinstance(kind, str) else int(kind),
+                             int(t_bins), int(sub_bins), int(grid_cells))
+    out = ctypes.c_void_p()
+    check(lib.ts_build_index(ctypes.byref(s), ctypes.byref(p), _current_stream(stream),
+                             ctypes.byref(out)))
+    del keep
+    return Index(out, int(s.n))
+
+
+def ts_index_get_info(index: Index) -> dict:
+    lib = _lib.load()
+    info = _lib.ts_index_info()
+    check(lib.ts_index_get_info(index.handle, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def ts_index_export(index: Index, field: str, dim: int = 0) -> np.ndarray:
+    lib = _lib.load()
+    fid = _lib.FIELDS[field]
+    size = ctypes.c_uint64(0)
+    st = lib.ts_index_export(index.handle, fid, dim, None, 0, ctypes.byref(size))
+    if st not in (_lib.TS_OK, 4):
+        check(st)
+    dtype = np.float64 if field in ("bin_start", "bin_end") else np.uint32
+    out = np.empty(int(size.value) // np.dtype(dtype).itemsize, dtype=dtype)
+    check(lib.ts_index_export(index.handle, fid, dim, out.ctypes.data if out.size else None,
+                              int(size.value), ctypes.byref(size)))
+    return out
+
+
+def _qparams(d, t_start, t_end, max_results):
+    return _lib.ts_query_params(float(d), float(t_start), float(t_end), int(max_results))
+
+
+def ts_schedule(index: Index, queries, d, t_start, t_end, stream=None):
+    lib = _lib.load()
+    s, keep = make_segments(queries)
+    n = int(s.n)
+    sel = np.zeros(n, dtype=np.int32)
+    lo = np.zeros(n, dtype=np.uint64)
+    hi = np.zeros(n, dtype=np.uint64)
+    qp = _qparams(d, t_start, t_end, 0)
+    check(lib.ts_schedule(index.handle, ctypes.byref(s), ctypes.byref(qp), _current_stream(stream),
+                          sel.ctypes.data, lo.ctypes.data, hi.ctypes.data))
+    del keep
+    return sel, lo, hi
+
+
+def ts_search(index: Index, queries, d, t_start, t_end, max_results=0, stream=None) -> Result:
+    """Search; raises TsError on failure. With max_results exceeded the returned Result has
+    status TS_ERR_CAPACITY (4), the exact count and no rows."""
+    lib = _lib.load()
+    s, keep = make_segments(queries)
+    qp = _qparams(d, t_start, t_end, max_results)
+    out = ctypes.c_void_p()
+    st = lib.ts_search(index.handle, ctypes.byref(s), ctypes.byref(qp), _current_stream(stream),
+                       ctypes.byref(out))
+    del keep
+    if st == 4 and out.value:
+        return Result(out, st)
+    check(st)
+    return Result(out, st)
+
+
+def ts_result_count(result: Result) -> int:
+    return result.count
+
+
+def ts_result_stats(result: Result) -> dict:
+    lib = _lib.load()
+    st = _lib.ts_search_stats()
+    check(lib.ts_result_stats(result.handle, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def ts_result_arrays(result: Result):
+    """Device pointers (ints) of q_idx, e_idx, t_in, t_out."""
+    lib = _lib.load()
+    ptrs = [ctypes.c_void_p() for _ in range(4)]
+    check(lib.ts_result_arrays(result.handle, *[ctypes.byref(p) for p in ptrs]))
+    return tuple(p.value for p in ptrs)
+
+
+def ts_result_copy_to_host(result: Result, stream=None, sort=False) -> dict:
+    lib = _lib.load()
+    n = result.count
+    q = np.empty(n, dtype=np.uint32)
+    e = np.empty(n, dtype=np.uint32)
+    tin = np.empty(n, dtype=np.float64)
+    tout = np.empty(n, dtype=np.float64)
+    if n:
+        check(lib.ts_result_copy_to_host(result.handle, q.ctypes.data, e.ctypes.data,
+                                         tin.ctypes.data, tout.ctypes.data,
+                                         _current_stream(stream)))
+    out = {"q_idx": q, "e_idx": e, "t_in": tin, "t_out": tout}
+    if sort and n:
+        order = np.lexsort((e, q))
+        out = {k: v[order] for k, v in out.items()}
+    return out
+
+
+def ts_free(obj):
+    obj.free()
+
+
+def ts_kernel_launches() -> int:
+    return int(_lib.load().ts_kernel_launches())
+
+
+def ts_last_error() -> str:
+    return _lib.load().ts_last_error().decode()

@@ -1,0 +1,259 @@
+// ts_api.cu -- the extern "C" boundary declared in include/ts.h.
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "ts_search.cuh"
+
+
+using namespace ts;
+
+struct ts_index {
+    Index ix;
+};
+
+struct ts_result {
+    uint32_t magic = MAGIC_RESULT;
+    cudaStream_t stream = nullptr;
+    SearchOut out;
+};
+
+namespace {
+
+ts_status clear_error(ts_status s)
+{
+    if (s == TS_OK) set_error("%s", "");
+    return s;
+}
+
+template <class F>
+ts_status guarded(F &&f)
+{
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return TS_ERR_OOM;
+    } catch (...) {
+        set_error("unexpected exception");
+        return TS_ERR_INTERNAL;
+    }
+}
+
+void free_result_arrays(ts_result *r)
+{
+    cudaStream_t s = r->stream;
+    if (r->out.q) cudaFreeAsync(r->out.q, s);
+    if (r->out.e) cudaFreeAsync(r->out.e, s);
+    if (r->out.tin) cudaFreeAsync(r->out.tin, s);
+    if (r->out.tout) cudaFreeAsync(r->out.tout, s);
+    r->out.q = r->out.e = nullptr;
+    r->out.tin = r->out.tout = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ts_version(void) { return "ts_gb300 0.1 (sm_103a)"; }
+
+const char *ts_last_error(void) { return ts::last_error(); }
+
+uint64_t ts_kernel_launches(void) { return (uint64_t)ts::launch_count(); }
+
+ts_status ts_build_index(const ts_segments *db, const ts_index_params *params, void *stream,
+                         ts_index **out)
+{
+    return guarded([&]() -> ts_status {
+        if (!out) {
+            set_error("ts_build_index: NULL out");
+            return TS_ERR_INVALID_ARG;
+        }
+        *out = nullptr;
+        Index *ix = nullptr;
+        ts_status st = build_index(db, params, (cudaStream_t)stream, &ix);
+        if (st != TS_OK) return st;
+        // Index is the first (only) member of ts_index: the handle is the Index object itself.
+        static_assert(sizeof(ts_index) == sizeof(Index), "handle layout");
+        *out = reinterpret_cast<ts_index *>(ix);
+        return clear_error(TS_OK);
+    });
+}
+
+ts_status ts_index_get_info(const ts_index *h, ts_index_info *info)
+{
+    const Index *ix = reinterpret_cast<const Index *>(h);
+    if (!ix || ix->magic != MAGIC_INDEX || !info) {
+        set_error("ts_index_get_info: invalid handle or NULL info");
+        return TS_ERR_INVALID_ARG;
+    }
+    memset(info, 0, sizeof(*info));
+    info->kind = ix->kind;
+    info->t_bins = ix->m;
+    for (int d = 0; d < 3; d++) {
+        info->sub_bins[d] = ix->v[d];
+        info->st_len[d] = ix->st_len[d];
+        info->sub_lo[d] = ix->sub_lo[d];
+        info->sub_w[d] = ix->sub_w[d];
+        info->grid_lo[d] = ix->g_lo[d];
+        info->grid_w[d] = ix->g_w[d];
+    }
+    info->grid_cells = ix->g;
+    info->n = ix->n;
+    info->grid_len = ix->g_len;
+    info->device_bytes = ix->bytes;
+    info->t_min = ix->tmin;
+    info->t_max = ix->tmax;
+    info->bin_width = ix->b;
+    return clear_error(TS_OK);
+}
+
+ts_status ts_index_export(const ts_index *h, int32_t field, int32_t dim, void *dst,
+                          uint64_t capacity, uint64_t *size)
+{
+    const Index *ix = reinterpret_cast<const Index *>(h);
+    if (!ix || ix->magic != MAGIC_INDEX) {
+        set_error("ts_index_export: invalid handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    const void *src = nullptr;
+    uint64_t bytes = 0;
+    bool dim_ok = dim >= 0 && dim < 3;
+    switch (field) {
+    case TS_FIELD_PERM: src = ix->orig; bytes = 4 * ix->n; break;
+    case TS_FIELD_BIN_START: src = ix->bin_start; bytes = 8ull * ix->m; break;
+    case TS_FIELD_BIN_END: src = ix->bin_end; bytes = 8ull * ix->m; break;
+    case TS_FIELD_BIN_OFF: src = ix->bin_off; bytes = 4ull * (ix->m + 1ull); break;
+    case TS_FIELD_ST_IDS:
+        if (!dim_ok || !ix->st_ids[dim]) break;
+        src = ix->st_ids[dim];
+        bytes = 4 * ix->st_len[dim];
+        break;
+    case TS_FIELD_ST_OFF:
+        if (!dim_ok || !ix->st_off[dim]) break;
+        src = ix->st_off[dim];
+        bytes = 4ull * ((uint64_t)ix->v[dim] * ix->m + 1ull);
+        break;
+    case TS_FIELD_GRID_A: src = ix->ga; bytes = 4 * ix->g_len; break;
+    case TS_FIELD_GRID_OFF:
+        src = ix->g_off;
+        bytes = ix->g_off ? 4ull * ((uint64_t)ix->g * ix->g * ix->g + 1ull) : 0;
+        break;
+    default: break;
+    }
+    if (!src) {
+        set_error("ts_index_export: field %d (dim %d) not present in this index", field, dim);
+        return TS_ERR_INVALID_ARG;
+    }
+    if (size) *size = bytes;
+    if (!dst || capacity < bytes) {
+        set_error("ts_index_export: capacity %llu below %llu bytes", (unsigned long long)capacity,
+                  (unsigned long long)bytes);
+        return TS_ERR_CAPACITY;
+    }
+    TS_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+    return clear_error(TS_OK);
+}
+
+ts_status ts_schedule(const ts_index *h, const ts_segments *q, const ts_query_params *qp,
+                      void *stream, int32_t *sel, uint64_t *lo, uint64_t *hi)
+{
+    const Index *ix = reinterpret_cast<const Index *>(h);
+    if (!ix || ix->magic != MAGIC_INDEX) {
+        set_error("ts_schedule: invalid index handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    return guarded([&]() -> ts_status {
+        ts_status st = schedule_only(ix, q, qp, (cudaStream_t)stream, sel, lo, hi);
+        return st == TS_OK ? clear_error(st) : st;
+    });
+}
+
+ts_status ts_search(const ts_index *h, const ts_segments *q, const ts_query_params *qp,
+                    void *stream, ts_result **out)
+{
+    const Index *ix = reinterpret_cast<const Index *>(h);
+    if (!ix || ix->magic != MAGIC_INDEX || !out) {
+        set_error("ts_search: invalid index handle or NULL out");
+        return TS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    return guarded([&]() -> ts_status {
+        ts_result *r = new ts_result();
+        r->stream = (cudaStream_t)stream;
+        ts_status st = search_plain(ix, q, qp, r->stream, &r->out);
+        if (st == TS_OK || st == TS_ERR_CAPACITY) {
+            *out = r;
+            return st == TS_OK ? clear_error(st) : st;
+        }
+        free_result_arrays(r);
+        delete r;
+        return st;
+    });
+}
+
+uint64_t ts_result_count(const ts_result *r)
+{
+    if (!r || r->magic != MAGIC_RESULT) return 0;
+    return r->out.count;
+}
+
+ts_status ts_result_arrays(const ts_result *r, const uint32_t **q_idx, const uint32_t **e_idx,
+                           const double **t_in, const double **t_out)
+{
+    if (!r || r->magic != MAGIC_RESULT) {
+        set_error("ts_result_arrays: invalid handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    if (q_idx) *q_idx = r->out.q;
+    if (e_idx) *e_idx = r->out.e;
+    if (t_in) *t_in = r->out.tin;
+    if (t_out) *t_out = r->out.tout;
+    return clear_error(TS_OK);
+}
+
+ts_status ts_result_stats(const ts_result *r, ts_search_stats *stats)
+{
+    if (!r || r->magic != MAGIC_RESULT || !stats) {
+        set_error("ts_result_stats: invalid handle or NULL stats");
+        return TS_ERR_INVALID_ARG;
+    }
+    *stats = r->out.stats;
+    return clear_error(TS_OK);
+}
+
+ts_status ts_result_copy_to_host(const ts_result *r, uint32_t *q_idx, uint32_t *e_idx,
+                                 double *t_in, double *t_out, void *stream)
+{
+    if (!r || r->magic != MAGIC_RESULT) {
+        set_error("ts_result_copy_to_host: invalid handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    const uint64_t n = r->out.count;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n && r->out.q) {
+        if (q_idx) TS_CUDA(cudaMemcpyAsync(q_idx, r->out.q, 4 * n, cudaMemcpyDeviceToHost, s));
+        if (e_idx) TS_CUDA(cudaMemcpyAsync(e_idx, r->out.e, 4 * n, cudaMemcpyDeviceToHost, s));
+        if (t_in) TS_CUDA(cudaMemcpyAsync(t_in, r->out.tin, 8 * n, cudaMemcpyDeviceToHost, s));
+        if (t_out) TS_CUDA(cudaMemcpyAsync(t_out, r->out.tout, 8 * n, cudaMemcpyDeviceToHost, s));
+    }
+    TS_CUDA(cudaStreamSynchronize(s));
+    return clear_error(TS_OK);
+}
+
+void ts_free(void *handle)
+{
+    if (!handle) return;
+    uint32_t magic = *reinterpret_cast<uint32_t *>(handle);
+    if (magic == MAGIC_INDEX) {
+        destroy_index(reinterpret_cast<Index *>(handle));
+    } else if (magic == MAGIC_RESULT) {
+        ts_result *r = reinterpret_cast<ts_result *>(handle);
+        free_result_arrays(r);
+        r->magic = 0;
+        delete r;
+    }
+}
+
+}  // extern "C"

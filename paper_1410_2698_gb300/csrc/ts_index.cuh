@@ -1,0 +1,71 @@
+// ts_index.cuh -- the resident index (Sec. 4.1-4.3 re-laid out for HBM).
+#pragma once
+
+#include <vector>
+
+#include "ts_internal.cuh"
+
+namespace ts {
+
+constexpr uint32_t MAGIC_INDEX = 0x54534958u;   // "TSIX"
+constexpr uint32_t MAGIC_RESULT = 0x54535253u;  // "TSRS"
+
+struct Index {
+    uint32_t magic = MAGIC_INDEX;
+    int kind = 0;
+    uint64_t n = 0;
+    int device = 0;
+
+    // entries in start-time order (Sec. 4.2: D sorted by t_start and renumbered)
+    SegD *seg = nullptr;     // exact FP64 data
+    RecF *rec = nullptr;     // FP32 prefilter records
+    uint32_t *orig = nullptr;  // sorted position -> caller's index
+
+    // extents (exact, from the ingest reductions)
+    double tmin = 0, tmax = 0, max_dur = 0;
+    double emin[3] = {0, 0, 0}, emax[3] = {0, 0, 0}, longest[3] = {0, 0, 0};
+
+    // temporal bins (Sec. 4.2)
+    uint32_t m = 0;
+    double b = 0;
+    double *bin_start = nullptr, *bin_end = nullptr, *bin_pmax = nullptr;  // m each
+    uint32_t *bin_off = nullptr;  // m + 1
+
+    // spatiotemporal subbins (Sec. 4.3): per dimension an id array in (subbin, bin, time) order,
+    // a duplicated prefilter record per id, and offsets off[j*m + i]
+    uint32_t v[3] = {0, 0, 0};
+    double sub_lo[3] = {0, 0, 0}, sub_w[3] = {0, 0, 0};
+    uint32_t *st_ids[3] = {nullptr, nullptr, nullptr};
+    RecF *st_rec[3] = {nullptr, nullptr, nullptr};
+    uint32_t *st_off[3] = {nullptr, nullptr, nullptr};
+    uint64_t st_len[3] = {0, 0, 0};
+
+    // flatly structured grid (Sec. 4.1): dense cell offsets over g^3 cells, lookup array A with a
+    // duplicated prefilter record per entry, and each entry's first cell (packed 3 x 10 bits)
+    uint32_t g = 0;
+    double g_lo[3] = {0, 0, 0}, g_w[3] = {0, 0, 0};
+    uint32_t *ga = nullptr;
+    RecF *ga_rec = nullptr;
+    uint32_t *g_off = nullptr;  // g^3 + 1
+    uint32_t *g_cell0 = nullptr;  // per sorted entry
+    uint64_t g_len = 0;
+
+    size_t bytes = 0;
+    std::vector<void *> allocs;
+
+    template <class T>
+    ts_status alloc(T **p, size_t count)
+    {
+        size_t nb = sizeof(T) * (count ? count : 1);
+        cudaError_t e = cudaMalloc((void **)p, nb);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            return cuda_status(e, "cudaMalloc(index)");
+        }
+        allocs.push_back((void *)*p);
+        bytes += nb;
+        return TS_OK;
+    }
+};
+
+}  // namespace ts

@@ -1,0 +1,195 @@
+// ts_internal.cuh -- shared declarations of the GB300 trajectory search library.
+//
+// Data layout in HBM (all arrays 256-byte aligned by cudaMalloc):
+//   SegD  : 64 B per entry, FP64 start point, start time, velocity, end time (exact test)
+//   RecF  : 32 B per entry, FP32 MBB rounded outward + start/end time rounded outward
+//           (conservative prefilter)
+//   Entries are stored in start-time order (Sec. 4.2); the spatiotemporal id arrays (Sec. 4.3)
+//   and the grid lookup array (Sec. 4.1) keep a duplicated RecF next to every id so candidate
+//   ranges stream contiguously.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <string>
+
+#include "../../include/ts.h"
+
+namespace ts {
+
+// ---------------------------------------------------------------------------------------------
+// records
+// ---------------------------------------------------------------------------------------------
+struct __align__(16) RecF {
+    float xmin, ymin, zmin, t0;  // t0 rounded toward -inf
+    float xmax, ymax, zmax, t1;  // t1 rounded toward +inf
+};
+static_assert(sizeof(RecF) == 32, "RecF is 32 bytes");
+
+struct __align__(16) SegD {
+    double x0, y0, z0, t0;
+    double vx, vy, vz, t1;
+};
+static_assert(sizeof(SegD) == 64, "SegD is 64 bytes");
+
+// Exact data of one query segment: start point and time, velocity, clipped window [w0, w1].
+struct __align__(16) QueryD {
+    double x0, y0, z0, t0;
+    double vx, vy, vz, w0;
+    double w1, pad;
+};
+static_assert(sizeof(QueryD) == 80, "QueryD is 80 bytes");
+
+// Query group: up to 32 consecutive (sorted) queries sharing one candidate array and range.
+struct Group {
+    uint32_t first;  // first sorted query
+    uint32_t count;  // 1..32
+    uint32_t sel;    // 0,1,2: X/Y/Z id array; 3: time-sorted entries; 4: grid lookup array
+    uint32_t lo, hi; // union of the members' candidate ranges [lo, hi)
+    uint32_t pad[3];
+};
+
+enum : uint32_t { SEL_X = 0, SEL_Y = 1, SEL_Z = 2, SEL_T = 3, SEL_GRID = 4 };
+
+// Status bits written by kernels (device status word).
+enum : uint32_t {
+    DEV_ERR_INVALID = 1u,   // NaN/Inf or t1 <= t0 in an input segment
+    DEV_ERR_TIMEOUT = 2u,   // a bounded wait ran out
+    DEV_ERR_INTERNAL = 4u,  // an internal consistency check failed
+    DEV_ERR_OVERFLOW = 8u   // a 32-bit offset would overflow
+};
+
+// Stats slots (u64 array in device memory).
+enum : int {
+    ST_QSEGS = 0, ST_TESTS = 1, ST_EXACT = 2, ST_HITS = 3, ST_TILES = 4, ST_GROUPS = 5,
+    ST_SUBBIN = 6, ST_NSLOTS = 8
+};
+
+// ---------------------------------------------------------------------------------------------
+// order-preserving integer keys of doubles (finite values; -0.0 canonicalised to +0.0)
+// ---------------------------------------------------------------------------------------------
+__host__ __device__ inline uint64_t dkey(double x)
+{
+    x = x + 0.0;  // -0.0 -> +0.0
+#ifdef __CUDA_ARCH__
+    uint64_t u = (uint64_t)__double_as_longlong(x);
+#else
+    uint64_t u;
+    memcpy(&u, &x, 8);
+#endif
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__host__ __device__ inline double dkey_inv(uint64_t k)
+{
+    uint64_t u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double x;
+    memcpy(&x, &u, 8);
+    return x;
+#endif
+}
+
+// ---------------------------------------------------------------------------------------------
+// 1-D uniform partition (subbins of Sec. 4.3, grid cells of Sec. 4.1): part j is
+// [lo + j*w, lo + (j+1)*w), the last part unbounded above. part_of(x) = largest j in [0, v-1]
+// with lo + j*w <= x, or -1 when x < lo. The boundaries are evaluated exactly as written
+// (library compiled without FMA contraction) so the part of a value never depends on rounding
+// of a division.
+// ---------------------------------------------------------------------------------------------
+__host__ __device__ inline double part_bound(double lo, double w, int j)
+{
+    return lo + (double)j * w;
+}
+
+__host__ __device__ inline int part_of(double x, double lo, double w, int v)
+{
+    if (!(x >= lo)) return -1;
+    if (v <= 1 || !(w > 0.0)) return v - 1;
+    double f = floor((x - lo) / w);
+    int j;
+    if (!(f < (double)v)) j = v - 1;
+    else if (f < 0.0) j = 0;
+    else j = (int)f;
+    while (j + 1 < v && part_bound(lo, w, j + 1) <= x) j++;
+    while (j > 0 && part_bound(lo, w, j) > x) j--;
+    return j;
+}
+
+// ---------------------------------------------------------------------------------------------
+// host-side error plumbing
+// ---------------------------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+ts_status cuda_status(cudaError_t e, const char *what);
+
+#define TS_CUDA(call)                                                                  \
+    do {                                                                               \
+        cudaError_t e__ = (call);                                                      \
+        if (e__ != cudaSuccess) return ::ts::cuda_status(e__, #call);                  \
+    } while (0)
+
+// Count one kernel launch of this library and surface launch errors.
+void note_launch();
+#define TS_LAUNCHED()                                                                  \
+    do {                                                                               \
+        ::ts::note_launch();                                                           \
+        TS_CUDA(cudaGetLastError());                                                   \
+    } while (0)
+
+#define TS_CHECK(st)                                                                   \
+    do {                                                                               \
+        ts_status s__ = (st);                                                          \
+        if (s__ != TS_OK) return s__;                                                  \
+    } while (0)
+
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), s(o.s) { o.p = nullptr; o.bytes = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept
+    {
+        if (this != &o) {
+            release();
+            p = o.p; bytes = o.bytes; s = o.s;
+            o.p = nullptr; o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release();
+    ts_status alloc(size_t nbytes, cudaStream_t stream);
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// ---------------------------------------------------------------------------------------------
+// primitives (ts_prims.cu)
+// ---------------------------------------------------------------------------------------------
+// exclusive scan of n u32 values into n+1 u64 offsets (out[n] = total)
+ts_status scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s);
+// exclusive scan of n u32 values into n+1 u32 offsets; sets DEV_ERR_OVERFLOW in *status when the
+// total does not fit in 32 bits
+ts_status scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *status,
+                   cudaStream_t s);
+// stable LSD radix sort of (key, value) pairs by the low `bits` bits of the key
+ts_status radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s);
+ts_status radix_sort_u32(uint32_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s);
+
+}  // namespace ts
+
+// Library-internal entry points shared between translation units.
+namespace ts {
+struct Index;
+struct SearchOut;
+ts_status build_index(const ts_segments *db, const ts_index_params *p, cudaStream_t s,
+                      Index **out);
+void destroy_index(Index *idx);
+}  // namespace ts

@@ -1,0 +1,331 @@
+// ts_prims.cu -- device primitives: exclusive scans and a stable LSD radix sort.
+//
+// Index building sorts segment keys and turns bin counts into offset arrays (radix sort plus
+// prefix sums, the GB300 form of the paper's sorted arrays and bin ranges, Sec. 4.1-4.3); the
+// search scans per-tile hit counts into output offsets. All of it is hand-written here.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <atomic>
+
+#include "ts_internal.cuh"
+
+namespace ts {
+
+// ---------------------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+const char *last_error() { return g_err; }
+
+ts_status cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        set_error("out of device memory in %s", what);
+        cudaGetLastError();
+        return TS_ERR_OOM;
+    }
+    set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
+    return TS_ERR_CUDA;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+}
+
+ts_status DevBuf::alloc(size_t nbytes, cudaStream_t stream)
+{
+    release();
+    s = stream;
+    bytes = nbytes;
+    if (nbytes == 0) nbytes = 256;
+    cudaError_t e = cudaMallocAsync(&p, nbytes, stream);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        return cuda_status(e, "cudaMallocAsync");
+    }
+    return TS_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// scan
+// ---------------------------------------------------------------------------------------------
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <class T>
+__device__ inline T warp_incl_scan(T v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive prefix, *total the sum.
+template <class T>
+__device__ inline T block_excl_scan(T v, T *total)
+{
+    __shared__ T warp_sums[SCAN_THREADS / 32 + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T incl = warp_incl_scan(v);
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        T w = lane < SCAN_THREADS / 32 ? warp_sums[lane] : T(0);
+        T wi = warp_incl_scan(w);
+        if (lane < SCAN_THREADS / 32) warp_sums[lane] = wi - w;
+        if (lane == SCAN_THREADS / 32 - 1) warp_sums[SCAN_THREADS / 32] = wi;  // total
+    }
+    __syncthreads();
+    T excl = warp_sums[wid] + incl - v;
+    if (total) *total = warp_sums[SCAN_THREADS / 32];
+    __syncthreads();
+    return excl;
+}
+
+template <class Tin, class Tout>
+__global__ void k_tile_sums(const Tin *in, uint64_t n, Tout *sums)
+{
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    Tout acc = 0;
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        uint64_t i = base + (uint64_t)k * SCAN_THREADS + threadIdx.x;
+        if (i < n) acc += (Tout)in[i];
+    }
+    Tout total;
+    block_excl_scan<Tout>(acc, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// Scan one tile per block with the tile's starting offset taken from `tile_off` (or 0), writing
+// out[i] = exclusive prefix; the last block also writes out[n] = total when tile_off holds the
+// grand total at index gridDim.x.
+template <class Tin, class Tout>
+__global__ void k_tile_scan(const Tin *in, uint64_t n, const Tout *tile_off, Tout *out)
+{
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    Tout v[SCAN_ITEMS];
+    Tout acc = 0;
+    // thread-contiguous items for a stable sequential order within a thread
+    uint64_t tbase = base + (uint64_t)threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        uint64_t i = tbase + k;
+        v[k] = i < n ? (Tout)in[i] : Tout(0);
+        acc += v[k];
+    }
+    Tout total;
+    Tout pre = block_excl_scan<Tout>(acc, &total);
+    Tout off = (tile_off ? tile_off[blockIdx.x] : Tout(0)) + pre;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        uint64_t i = tbase + k;
+        if (i < n) out[i] = off;
+        off += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+        out[n] = (tile_off ? tile_off[blockIdx.x] : Tout(0)) + total;
+}
+
+template <class Tin, class Tout>
+static ts_status scan_impl(const Tin *in, Tout *out, uint64_t n, cudaStream_t s)
+{
+    if (n == 0) {
+        TS_CUDA(cudaMemsetAsync(out, 0, sizeof(Tout), s));
+        return TS_OK;
+    }
+    uint64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nt == 1) {
+        k_tile_scan<Tin, Tout><<<1, SCAN_THREADS, 0, s>>>(in, n, nullptr, out);
+        TS_LAUNCHED();
+        return TS_OK;
+    }
+    DevBuf sums, offs;
+    TS_CHECK(sums.alloc(sizeof(Tout) * nt, s));
+    TS_CHECK(offs.alloc(sizeof(Tout) * (nt + 1), s));
+    k_tile_sums<Tin, Tout><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, sums.as<Tout>());
+    TS_LAUNCHED();
+    TS_CHECK((scan_impl<Tout, Tout>(sums.as<Tout>(), offs.as<Tout>(), nt, s)));
+    k_tile_scan<Tin, Tout><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, offs.as<Tout>(), out);
+    TS_LAUNCHED();
+    return TS_OK;
+}
+
+ts_status scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s)
+{
+    return scan_impl<uint32_t, uint64_t>(in, out, n, s);
+}
+
+__global__ void k_narrow_u64(const uint64_t *in, uint32_t *out, uint64_t n, uint32_t *status)
+{
+    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    uint64_t v = in[i];
+    if (v > 0xffffffffull) {
+        atomicOr(status, DEV_ERR_OVERFLOW);
+        v = 0xffffffffull;
+    }
+    out[i] = (uint32_t)v;
+}
+
+ts_status scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *status,
+                   cudaStream_t s)
+{
+    DevBuf wide;
+    TS_CHECK(wide.alloc(sizeof(uint64_t) * (n + 1), s));
+    TS_CHECK(scan_u32_to_u64(in, wide.as<uint64_t>(), n, s));
+    k_narrow_u64<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(wide.as<uint64_t>(), out, n,
+                                                                   status);
+    TS_LAUNCHED();
+    return TS_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// radix sort: LSD, 8-bit digits, 256 threads x 8 keys per block tile. Each pass: per-tile digit
+// histograms (digit-major), an exclusive scan of them, and a stable scatter in which every warp
+// ranks its 256 consecutive keys with __match_any_sync and the block adds the earlier warps'
+// counts.
+// ---------------------------------------------------------------------------------------------
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_RADIX = 256;
+
+template <class K>
+__global__ void k_rs_hist(const K *keys, uint64_t n, int shift, uint32_t *hist, uint32_t ntiles)
+{
+    __shared__ uint32_t h[RS_RADIX];
+    for (int i = threadIdx.x; i < RS_RADIX; i += RS_THREADS) h[i] = 0;
+    __syncthreads();
+    uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+    for (int k = 0; k < RS_ITEMS; k++) {
+        uint64_t i = base + (uint64_t)k * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int dgt = threadIdx.x; dgt < RS_RADIX; dgt += RS_THREADS)
+        hist[(uint64_t)dgt * ntiles + blockIdx.x] = h[dgt];
+}
+
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K *keys_in, const uint32_t *vals_in,
+                                                           K *keys_out, uint32_t *vals_out,
+                                                           uint64_t n, int shift,
+                                                           const uint64_t *digit_off,
+                                                           uint32_t ntiles)
+{
+    __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * RS_RADIX; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t wbase = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)wid * (RS_ITEMS * 32);
+    K key[RS_ITEMS];
+    uint32_t val[RS_ITEMS];
+    uint32_t rank[RS_ITEMS];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; k++) {
+        uint64_t i = wbase + (uint64_t)k * 32 + lane;
+        bool ok = i < n;
+        key[k] = ok ? keys_in[i] : K(0);
+        val[k] = ok ? vals_in[i] : 0u;
+        uint32_t dgt = ok ? ((uint32_t)(key[k] >> shift) & 0xffu) : 0x100u;
+        uint32_t peers = __match_any_sync(0xffffffffu, dgt);
+        uint32_t before = __popc(peers & lt_mask);
+        uint32_t leader = __ffs(peers) - 1;
+        uint32_t cur = 0;
+        if (ok && lane == (int)leader) {
+            cur = wcnt[wid][dgt];
+            wcnt[wid][dgt] = cur + __popc(peers);
+        }
+        cur = __shfl_sync(0xffffffffu, cur, leader);
+        rank[k] = cur + before;
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over warps, per digit
+    for (int dgt = threadIdx.x; dgt < RS_RADIX; dgt += RS_THREADS) {
+        uint32_t run = 0;
+        for (int w = 0; w < RS_WARPS; w++) {
+            uint32_t c = wcnt[w][dgt];
+            wcnt[w][dgt] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; k++) {
+        uint64_t i = wbase + (uint64_t)k * 32 + lane;
+        if (i >= n) continue;
+        uint32_t dgt = (uint32_t)(key[k] >> shift) & 0xffu;
+        uint64_t dst = digit_off[(uint64_t)dgt * ntiles + blockIdx.x] + wcnt[wid][dgt] + rank[k];
+        keys_out[dst] = key[k];
+        vals_out[dst] = val[k];
+    }
+}
+
+template <class K>
+static ts_status radix_sort_impl(K *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s)
+{
+    if (n <= 1 || bits <= 0) return TS_OK;
+    uint32_t ntiles = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
+    DevBuf kb, vb, hist, off;
+    TS_CHECK(kb.alloc(sizeof(K) * n, s));
+    TS_CHECK(vb.alloc(sizeof(uint32_t) * n, s));
+    uint64_t nh = (uint64_t)RS_RADIX * ntiles;
+    TS_CHECK(hist.alloc(sizeof(uint32_t) * nh, s));
+    TS_CHECK(off.alloc(sizeof(uint64_t) * (nh + 1), s));
+    K *ka = keys, *kbp = kb.as<K>();
+    uint32_t *va = vals, *vbp = vb.as<uint32_t>();
+    int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; p++) {
+        int shift = 8 * p;
+        k_rs_hist<K><<<ntiles, RS_THREADS, 0, s>>>(ka, n, shift, hist.as<uint32_t>(), ntiles);
+        TS_LAUNCHED();
+        TS_CHECK(scan_u32_to_u64(hist.as<uint32_t>(), off.as<uint64_t>(), nh, s));
+        k_rs_scatter<K><<<ntiles, RS_THREADS, 0, s>>>(ka, va, kbp, vbp, n, shift,
+                                                      off.as<uint64_t>(), ntiles);
+        TS_LAUNCHED();
+        K *tk = ka; ka = kbp; kbp = tk;
+        uint32_t *tv = va; va = vbp; vbp = tv;
+    }
+    if (ka != keys) {
+        TS_CUDA(cudaMemcpyAsync(keys, ka, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
+        TS_CUDA(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return TS_OK;
+}
+
+ts_status radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s)
+{
+    return radix_sort_impl<uint64_t>(keys, vals, n, bits, s);
+}
+
+ts_status radix_sort_u32(uint32_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s)
+{
+    return radix_sort_impl<uint32_t>(keys, vals, n, bits, s);
+}
+
+}  // namespace ts

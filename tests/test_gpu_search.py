@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, on seeded inputs."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_2698_gb300 import api, workloads
+from paper_1410_2698_gb300.workloads import Segments
+from tests import parity
+from tests.cases import seg, segset
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return workloads.tiny()
+
+
+def _run(db, q, kind, d, Ts, Te, **kw):
+    idx = api.ts_build_index(db, kind=kind, **kw)
+    res = api.ts_search(idx, q, d, Ts, Te)
+    got = res.to_host(sort=True)
+    stats = res.stats
+    info = idx.info()
+    res.free()
+    idx.free()
+    return got, stats, info
+
+
+@pytest.mark.parametrize("kind,kw", [
+    ("brute", {}),
+    ("temporal", {}),
+    ("temporal", {"t_bins": 1}),
+    ("temporal", {"t_bins": 37}),
+    ("temporal", {"t_bins": 20000}),
+    ("spatiotemporal", {}),
+    ("spatiotemporal", {"sub_bins": 1}),
+    ("spatiotemporal", {"sub_bins": 3, "t_bins": 11}),
+    ("spatiotemporal", {"sub_bins": 64}),
+])
+def test_tiny_config_matches_oracle(tiny, kind, kw):
+    d = tiny.distances[0]
+    ref = oracle.search(tiny.db, tiny.queries, tiny.t_start, tiny.t_end, d)
+    got, stats, _ = _run(tiny.db, tiny.queries, kind, d, tiny.t_start, tiny.t_end, **kw)
+    diag = parity.compare(got, ref, tiny.db, tiny.queries, tiny.t_start, tiny.t_end, d)
+    assert diag["rows"] > 1000
+    assert stats["n_hits"] == got["q_idx"].size
+    assert stats["n_qsegs"] == 2000 - int(np.sum(np.minimum(tiny.queries.t1, tiny.t_end)
+                                                 <= np.maximum(tiny.queries.t0, tiny.t_start)))
+    assert stats["n_exact"] <= stats["n_tests"]
+    if kind == "brute":
+        assert stats["n_tests"] == stats["n_qsegs"] * tiny.db.n
+
+
+def test_results_are_bit_identical_to_the_oracle_when_no_pair_is_near_tangent(tiny):
+    d = 5.0
+    ref = oracle.search(tiny.db, tiny.queries, tiny.t_start, tiny.t_end, d)
+    got, _, _ = _run(tiny.db, tiny.queries, "temporal", d, tiny.t_start, tiny.t_end)
+    diag = parity.compare(got, ref, tiny.db, tiny.queries, tiny.t_start, tiny.t_end, d)
+    if diag["exempt"] == 0:
+        assert diag["bit_exact"]
+
+
+def test_deterministic_order(tiny):
+    idx = api.ts_build_index(tiny.db, kind="spatiotemporal")
+    a = api.ts_search(idx, tiny.queries, 5.0, 0, 70).to_host()
+    b = api.ts_search(idx, tiny.queries, 5.0, 0, 70).to_host()
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+
+
+def test_temporal_index_worked_example_on_gpu():
+    with open(os.path.join(GOLDEN, "temporal_index_example.json")) as f:
+        g = json.load(f)
+    t = np.array(g["segments_t_start_t_end"])
+    rows = [seg((0, 0, 0), a, (1, 1, 1), b) for a, b in t]
+    idx = api.ts_build_index(segset(rows), kind="temporal", t_bins=g["m"])
+    exp = g["expected"]
+    np.testing.assert_array_equal(api.ts_index_export(idx, "perm"), np.arange(15))
+    np.testing.assert_array_equal(api.ts_index_export(idx, "bin_start"), exp["bin_start"])
+    np.testing.assert_array_equal(api.ts_index_export(idx, "bin_end"), exp["bin_end"])
+    off = api.ts_index_export(idx, "bin_off")
+    np.testing.assert_array_equal(off[:-1], exp["bin_first"])
+    np.testing.assert_array_equal(off[1:] - 1, exp["bin_last"])
+
+
+@pytest.mark.parametrize("m", [1, 7, 100, 997])
+def test_temporal_index_matches_oracle(tiny, m):
+    db = tiny.db
+    idx = api.ts_build_index(db, kind="temporal", t_bins=m)
+    ref = oracle.temporal_index(db.t0, db.t1, m)
+    np.testing.assert_array_equal(api.ts_index_export(idx, "perm"), ref["perm"])
+    np.testing.assert_array_equal(api.ts_index_export(idx, "bin_start"), ref["bin_start"])
+    np.testing.assert_array_equal(api.ts_index_export(idx, "bin_end"), ref["bin_end"])
+    np.testing.assert_array_equal(api.ts_index_export(idx, "bin_off"), ref["bin_off"])
+    info = idx.info()
+    assert info["t_min"] == ref["tmin"] and info["bin_width"] == ref["b"]
+
+
+@pytest.mark.parametrize("v", [1, 5, 16])
+def test_spatiotemporal_index_matches_oracle(tiny, v):
+    db = tiny.db
+    m = 50
+    idx = api.ts_build_index(db, kind="spatiotemporal", t_bins=m, sub_bins=v)
+    info = idx.info()
+    tref = oracle.temporal_index(db.t0, db.t1, m)
+    perm = tref["perm"]
+    lo_cols = [np.minimum(db.x0, db.x1), np.minimum(db.y0, db.y1), np.minimum(db.z0, db.z1)]
+    hi_cols = [np.maximum(db.x0, db.x1), np.maximum(db.y0, db.y1), np.maximum(db.z0, db.z1)]
+    for dim in range(3):
+        lo, w, ve = oracle.st_params(lo_cols[dim], hi_cols[dim], v)
+        assert (info["sub_lo"][dim], info["sub_w"][dim], info["sub_bins"][dim]) == (lo, w, ve)
+        ids, off = oracle.st_dim(lo_cols[dim][perm], hi_cols[dim][perm], tref["bin_of"], m, lo,
+                                 w, ve)
+        np.testing.assert_array_equal(api.ts_index_export(idx, "st_ids", dim), ids)
+        np.testing.assert_array_equal(api.ts_index_export(idx, "st_off", dim), off)
+
+
+def test_schedules_match_oracle(tiny):
+    db, q = tiny.db, tiny.queries
+    d, Ts, Te = 5.0, 0.0, 70.0
+    m = 200
+    w0 = np.maximum(q.t0, Ts)
+    w1 = np.minimum(q.t1, Te)
+    tref = oracle.temporal_index(db.t0, db.t1, m)
+    idx = api.ts_build_index(db, kind="temporal", t_bins=m)
+    sel, lo, hi = api.ts_schedule(idx, q, d, Ts, Te)
+    rlo, rhi = oracle.temporal_schedule(tref, w0, w1)
+    np.testing.assert_array_equal(lo, rlo)
+    np.testing.assert_array_equal(hi, rhi)
+    assert np.all(sel == 3)
+    # spatiotemporal
+    idx = api.ts_build_index(db, kind="spatiotemporal", t_bins=m, sub_bins=8)
+    info = idx.info()
+    dims = []
+    lo_cols = [np.minimum(db.x0, db.x1), np.minimum(db.y0, db.y1), np.minimum(db.z0, db.z1)]
+    hi_cols = [np.maximum(db.x0, db.x1), np.maximum(db.y0, db.y1), np.maximum(db.z0, db.z1)]
+    for dim in range(3):
+        ids, off = oracle.st_dim(lo_cols[dim][tref["perm"]], hi_cols[dim][tref["perm"]],
+                                 tref["bin_of"], m, info["sub_lo"][dim], info["sub_w"][dim],
+                                 info["sub_bins"][dim])
+        dims.append({"lo": info["sub_lo"][dim], "w": info["sub_w"][dim],
+                     "v": info["sub_bins"][dim], "off": off})
+    qmin = [np.minimum(q.x0, q.x1), np.minimum(q.y0, q.y1), np.minimum(q.z0, q.z1)]
+    qmax = [np.maximum(q.x0, q.x1), np.maximum(q.y0, q.y1), np.maximum(q.z0, q.z1)]
+    rsel, rlo, rhi = oracle.st_schedule(tref, dims, qmin, qmax, w0, w1, d)
+    sel, lo, hi = api.ts_schedule(idx, q, d, Ts, Te)
+    np.testing.assert_array_equal(sel, rsel)
+    np.testing.assert_array_equal(lo, rlo)
+    np.testing.assert_array_equal(hi, rhi)
+    assert (rsel < 3).sum() > 100  # some queries served by subbins
+
+
+def test_analytic_cases_on_gpu():
+    # head-on (hit [7.5, 12.5]), parallel at 0.999 d (whole window), perpendicular tangent
+    # (single instant 10), parallel at 1.001 d (no hit), touching windows (no hit)
+    d = 5.0
+    q = segset([seg((-10, 0, 0), 0, (10, 0, 0), 20)])
+    e = segset([
+        seg((10, 0, 0), 0, (-10, 0, 0), 20),
+        seg((-10, 4.995, 0), 0, (10, 4.995, 0), 20),
+        seg((0, 5, 0), 0, (0, 5, 0), 20),
+        seg((-10, 5.005, 0), 0, (10, 5.005, 0), 20),
+        seg((10, 0, 0), 20, (11, 0, 0), 21),
+    ])
+    for kind in ("brute", "temporal", "spatiotemporal"):
+        idx = api.ts_build_index(e, kind=kind)
+        got = api.ts_search(idx, q, d, -1e9, 1e9).to_host(sort=True)
+        assert got["e_idx"].tolist() == [0, 1, 2], kind
+        np.testing.assert_allclose(got["t_in"], [7.5, 0.0, 10.0], atol=1e-12)
+        np.testing.assert_allclose(got["t_out"], [12.5, 20.0, 10.0], atol=1e-12)
+
+
+def test_edge_cases():
+    rng = np.random.default_rng(3)
+    from tests.cases import random_segments
+    db = random_segments(rng, 300, box=5.0)
+    q = random_segments(rng, 50, box=5.0)
+    idx = api.ts_build_index(db, kind="spatiotemporal")
+    # empty query set
+    empty = Segments.from_matrix(np.zeros((0, 8)))
+    r = api.ts_search(idx, empty, 1.0, 0, 10)
+    assert r.count == 0 and r.stats["n_queries"] == 0
+    # interval outside every query window
+    r = api.ts_search(idx, q, 1.0, 100.0, 200.0)
+    assert r.count == 0 and r.stats["n_qsegs"] == 0
+    # degenerate interval (t_start == t_end): no positive overlap anywhere
+    r = api.ts_search(idx, q, 1.0, 5.0, 5.0)
+    assert r.count == 0
+    # huge d: every pair with a positive-length window is a hit
+    ref = oracle.search(db, q, -1e9, 1e9, 1e6)
+    got = api.ts_search(idx, q, 1e6, -1e9, 1e9).to_host(sort=True)
+    parity.compare(got, ref, db, q, -1e9, 1e9, 1e6)
+    # single-entry database
+    one = db.take([7])
+    idx1 = api.ts_build_index(one, kind="temporal")
+    ref = oracle.search(one, q, 0, 20, 3.0)
+    got = api.ts_search(idx1, q, 3.0, 0, 20).to_host(sort=True)
+    parity.compare(got, ref, one, q, 0, 20, 3.0)
+
+
+def test_invalid_inputs_are_rejected():
+    rng = np.random.default_rng(4)
+    from tests.cases import random_segments
+    db = random_segments(rng, 100)
+    bad = db.as_matrix().copy()
+    bad[5, 2] = np.nan
+    with pytest.raises(api.TsError) as e:
+        api.ts_build_index(Segments.from_matrix(bad), kind="temporal")
+    assert e.value.status == 1
+    bad = db.as_matrix().copy()
+    bad[3, 7] = bad[3, 3]  # t_end == t_start
+    with pytest.raises(api.TsError):
+        api.ts_build_index(Segments.from_matrix(bad), kind="temporal")
+    idx = api.ts_build_index(db, kind="temporal")
+    for d in (0.0, -1.0, float("inf"), float("nan")):
+        with pytest.raises(api.TsError):
+            api.ts_search(idx, db, d, 0, 10)
+    with pytest.raises(api.TsError):
+        api.ts_search(idx, db, 1.0, 10, 0)
+    qbad = db.as_matrix().copy()
+    qbad[0, 0] = np.inf
+    with pytest.raises(api.TsError):
+        api.ts_search(idx, Segments.from_matrix(qbad), 1.0, 0, 10)
+
+
+def test_result_capacity_reports_exact_count(tiny):
+    idx = api.ts_build_index(tiny.db, kind="temporal")
+    full = api.ts_search(idx, tiny.queries, 5.0, 0, 70)
+    n = full.count
+    capped = api.ts_search(idx, tiny.queries, 5.0, 0, 70, max_results=n - 1)
+    assert capped.status == 4 and capped.count == n
+    ok = api.ts_search(idx, tiny.queries, 5.0, 0, 70, max_results=n)
+    assert ok.status == 0 and ok.count == n
+
+
+def test_device_tensor_inputs(tiny):
+    import torch
+    cols = {f: torch.from_numpy(getattr(tiny.db, f)).cuda() for f in Segments.FIELDS}
+    qcols = {f: torch.from_numpy(getattr(tiny.queries, f)).cuda() for f in Segments.FIELDS}
+    idx = api.ts_build_index(cols, kind="spatiotemporal")
+    got = api.ts_search(idx, qcols, 5.0, 0, 70).to_host(sort=True)
+    ref = oracle.search(tiny.db, tiny.queries, 0, 70, 5.0)
+    parity.compare(got, ref, tiny.db, tiny.queries, 0, 70, 5.0)
