@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="random-walk-1m")
-    ap.add_argument("--indexes", default="spatiotemporal,temporal")
+    ap.add_argument("--indexes", default="spatiotemporal,temporal,spatial")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()

@@ -76,6 +76,11 @@ def _load():
             lib.orc_fsg_candidates.argtypes = [_I64, _P, _P, _I32, _P, _P, _P, _P, _I64, _P, _P,
                                                _D, _P, _P]
             lib.orc_fsg_candidates.restype = None
+            lib.orc_grid1.argtypes = [_I64, _P, _I32, _P, _P, _P, _P]
+            lib.orc_grid1.restype = _I64
+            lib.orc_grid1_candidates.argtypes = [_I32, _P, _P, _P, _P, _I64, _P, _P, _P, _P, _D,
+                                                 _P, _P]
+            lib.orc_grid1_candidates.restype = None
             _lib = lib
     return _lib
 
@@ -302,3 +307,37 @@ def fsg_candidates(emin3, emax3, g, lo3, w3, A, off, qmin3, qmax3, d):
                            _ptr(lo), _ptr(w), _ptr(A), _ptr(off), nq, ctypes.cast(qa, _P),
                            ctypes.cast(qb, _P), d, _ptr(raw), _ptr(uniq))
     return raw, uniq
+
+
+def grid1(emin3, g, lo3, w3):
+    """One-cell-per-entry grid (Sec. 4.1 grid, entries keyed by their MBB minimum corner):
+    lookup array A and per-cell offsets (g^3 + 1)."""
+    lib = _load()
+    emin = [_f64(a) for a in emin3]
+    n = emin[0].shape[0]
+    ea = (ctypes.c_void_p * 3)(*[a.ctypes.data for a in emin])
+    lo, w = _f64(lo3), _f64(w3)
+    off = np.empty(g * g * g + 1, dtype=np.int64)
+    A = np.empty(max(n, 1), dtype=np.uint32)
+    ln = lib.orc_grid1(n, ctypes.cast(ea, _P), g, _ptr(lo), _ptr(w), _ptr(A), _ptr(off))
+    if ln < 0:
+        raise MemoryError("oracle allocation failed")
+    return A[:n], off
+
+
+def grid1_candidates(g, lo3, w3, longest3, off, qmin3, qmax3, w0, w1, d):
+    """Per query: (number of z-runs, number of candidates) in the one-cell-per-entry grid."""
+    lib = _load()
+    qmin = [_f64(a) for a in qmin3]
+    qmax = [_f64(a) for a in qmax3]
+    qa = (ctypes.c_void_p * 3)(*[a.ctypes.data for a in qmin])
+    qb = (ctypes.c_void_p * 3)(*[a.ctypes.data for a in qmax])
+    lo, w, L = _f64(lo3), _f64(w3), _f64(longest3)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    w0, w1 = _f64(w0), _f64(w1)
+    nq = w0.shape[0]
+    runs = np.empty(nq, dtype=np.int64)
+    cand = np.empty(nq, dtype=np.int64)
+    lib.orc_grid1_candidates(g, _ptr(lo), _ptr(w), _ptr(L), _ptr(off), nq, ctypes.cast(qa, _P),
+                             ctypes.cast(qb, _P), _ptr(w0), _ptr(w1), d, _ptr(runs), _ptr(cand))
+    return runs, cand

@@ -42,6 +42,9 @@ static void seg_load(const double *const *f, int64_t i, orc_seg *s)
 }
 
 static double dmax(double a, double b) { return a > b ? a : b; }
+
+/* relative widening of the d-expanded query extents before they are mapped to subbins or cells */
+#define EXT_SLACK 1e-12
 static double dmin(double a, double b) { return a < b ? a : b; }
 
 /*
@@ -497,7 +500,10 @@ void orc_st_schedule(int32_t m, const double *bin_start, const double *bin_end,
         hi[k] = bin_off[jh + 1];
         int64_t best = -1;
         for (int dim = 0; dim < 3; dim++) {
-            double a = qmin[dim][k] - d, b = qmax[dim][k] + d;
+            /* d-expanded extent, widened by a relative 1e-12 so that rounding of min - d
+             * cannot move the extent past a subbin boundary it truly crosses */
+            double a = (qmin[dim][k] - d) - EXT_SLACK * (fabs(qmin[dim][k]) + d);
+            double b = (qmax[dim][k] + d) + EXT_SLACK * (fabs(qmax[dim][k]) + d);
             int32_t v = sub_v[dim];
             int32_t pa = part_of(a, sub_lo[dim], sub_w[dim], v);
             int32_t pb = part_of(b, sub_lo[dim], sub_w[dim], v);
@@ -625,5 +631,79 @@ void orc_fsg_candidates(int64_t n, const double *const *emin, const double *cons
         (void)n;
         n_raw[k] = raw;
         n_unique[k] = uniq;
+    }
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Flatly structured grid with one cell per entry (the Sec. 4.1 grid, each entry listed once in
+ * the cell that holds its MBB's minimum corner, so the candidate list of a query is duplicate-free
+ * without filtering): A holds, cell by cell in increasing h = (cx*g + cy)*g + cz, the (time-sorted)
+ * positions of the entries of that cell in increasing order; off[h] .. off[h+1]-1 is cell h's
+ * range. emin: 3 pointers (x, y, z), entries in sorted order. Returns n.
+ * ------------------------------------------------------------------------------------------- */
+int64_t orc_grid1(int64_t n, const double *const *emin, int32_t g, const double *lo,
+                  const double *w, uint32_t *A, int64_t *off)
+{
+    int64_t ncell = (int64_t)g * g * g;
+    int64_t *cell = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!cell) return -1;
+    for (int64_t h = 0; h <= ncell; h++) off[h] = 0;
+    for (int64_t s = 0; s < n; s++) {
+        int32_t c[3];
+        for (int dim = 0; dim < 3; dim++) {
+            int32_t a = part_of(emin[dim][s], lo[dim], w[dim], g);
+            c[dim] = a < 0 ? 0 : a;
+        }
+        cell[s] = ((int64_t)c[0] * g + c[1]) * g + c[2];
+        off[cell[s] + 1]++;
+    }
+    for (int64_t h = 0; h < ncell; h++) off[h + 1] += off[h];
+    int64_t *fill = malloc(sizeof(int64_t) * (size_t)ncell);
+    if (!fill) {
+        free(cell);
+        return -1;
+    }
+    memcpy(fill, off, sizeof(int64_t) * (size_t)ncell);
+    for (int64_t s = 0; s < n; s++) A[fill[cell[s]]++] = (uint32_t)s;
+    free(fill);
+    free(cell);
+    return n;
+}
+
+/*
+ * Candidates of a query in the one-cell-per-entry grid: an entry within d of the query has its
+ * MBB minimum corner in [qmin - d - longest, qmax + d] per axis (longest = the largest extent of
+ * an entry along that axis), widened by a relative 1e-12 against rounding. The cells meeting that
+ * box are read as z-runs, one per (cx, cy). Per query (window [w0, w1] must have positive length,
+ * else 0): the number of runs and of candidates (the runs' total length).
+ */
+void orc_grid1_candidates(int32_t g, const double *lo, const double *w, const double *longest,
+                          const int64_t *off, int64_t nq, const double *const *qmin,
+                          const double *const *qmax, const double *w0, const double *w1, double d,
+                          int64_t *n_runs, int64_t *n_cand)
+{
+    for (int64_t k = 0; k < nq; k++) {
+        n_runs[k] = 0;
+        n_cand[k] = 0;
+        if (!(w0[k] < w1[k])) continue;
+        int32_t ca[3], cb[3];
+        int empty = 0;
+        for (int dim = 0; dim < 3; dim++) {
+            double a = ((qmin[dim][k] - d) - longest[dim]) -
+                       EXT_SLACK * ((fabs(qmin[dim][k]) + d) + longest[dim]);
+            double b = (qmax[dim][k] + d) + EXT_SLACK * (fabs(qmax[dim][k]) + d);
+            int32_t pa = part_of(a, lo[dim], w[dim], g);
+            int32_t pb = part_of(b, lo[dim], w[dim], g);
+            ca[dim] = pa < 0 ? 0 : pa;
+            cb[dim] = pb;
+            if (pb < ca[dim]) empty = 1;
+        }
+        if (empty) continue;
+        n_runs[k] = (int64_t)(cb[0] - ca[0] + 1) * (cb[1] - ca[1] + 1);
+        for (int32_t cx = ca[0]; cx <= cb[0]; cx++)
+            for (int32_t cy = ca[1]; cy <= cb[1]; cy++) {
+                int64_t row = ((int64_t)cx * g + cy) * g;
+                n_cand[k] += off[row + cb[2] + 1] - off[row + ca[2]];
+            }
     }
 }

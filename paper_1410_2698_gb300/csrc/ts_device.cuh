@@ -1,0 +1,165 @@
+// ts_device.cuh -- device helpers of the pair test: PTX wrappers for the bulk-copy engine and
+// mbarriers, the exact FP64 interaction test and the conservative FP32 filter.
+#pragma once
+
+#include "ts_internal.cuh"
+
+namespace ts {
+
+// ---------------------------------------------------------------------------------------------
+// PTX wrappers: mbarrier + 1-D bulk copy (TMA engine), globaltimer
+// ---------------------------------------------------------------------------------------------
+static __device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+static __device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+static __device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+static __device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+static __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+static __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+static __device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2 s of wall time.
+static __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0 && globaltimer_ns() - t0 > 2000000000ull) return false;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// exact FP64 interaction test (same operation order as the plain definition; no contraction)
+// ---------------------------------------------------------------------------------------------
+static __device__ __forceinline__ double dmx(double a, double b) { return a > b ? a : b; }
+static __device__ __forceinline__ double dmn(double a, double b) { return a < b ? a : b; }
+
+struct Quad {
+    double t_lo, T, a, b, c;
+};
+
+// Window and quadratic coefficients; false when the common window has no positive length.
+static __device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e, double dd, Quad &o)
+{
+    double t_lo = dmx(q.w0, e.t0);
+    double t_hi = dmn(q.w1, e.t1);
+    if (!(t_lo < t_hi)) return false;
+    double dq = t_lo - q.t0, de = t_lo - e.t0;
+    double rx = (q.x0 + q.vx * dq) - (e.x0 + e.vx * de);
+    double ry = (q.y0 + q.vy * dq) - (e.y0 + e.vy * de);
+    double rz = (q.z0 + q.vz * dq) - (e.z0 + e.vz * de);
+    double dvx = q.vx - e.vx, dvy = q.vy - e.vy, dvz = q.vz - e.vz;
+    o.t_lo = t_lo;
+    o.T = t_hi - t_lo;
+    o.a = (dvx * dvx + dvy * dvy) + dvz * dvz;
+    o.b = (rx * dvx + ry * dvy) + rz * dvz;
+    o.c = ((rx * rx + ry * ry) + rz * rz) - dd;
+    return true;
+}
+
+// Division-free hit decision: the minimum of a tau^2 + 2 b tau + c over [0, T] is <= 0.
+static __device__ __forceinline__ bool quad_hit(const Quad &k)
+{
+    if (k.a == 0.0) return k.c <= 0.0;
+    if (k.b >= 0.0) return k.c <= 0.0;                       // minimum at tau = 0
+    if (-k.b >= k.a * k.T) return (k.a * k.T + 2.0 * k.b) * k.T + k.c <= 0.0;  // at tau = T
+    return k.b * k.b - k.a * k.c >= 0.0;                     // interior minimum
+}
+
+// Interval of a hit from the numerically stable root pair s/a, c/s.
+static __device__ __forceinline__ void quad_interval(const Quad &k, double *tin, double *tout)
+{
+    double lower, upper;
+    if (k.a == 0.0) {
+        lower = 0.0;
+        upper = k.T;
+    } else {
+        double disc = k.b * k.b - k.a * k.c;
+        if (disc < 0.0) disc = 0.0;  // only reachable within rounding of a tangency
+        double sq = sqrt(disc);
+        double s = -(k.b + copysign(sq, k.b));
+        double r1, r2;
+        if (s == 0.0) {
+            r1 = 0.0;
+            r2 = 0.0;
+        } else {
+            r1 = s / k.a;
+            r2 = k.c / s;
+        }
+        lower = dmx(0.0, dmn(r1, r2));
+        upper = dmn(k.T, dmx(r1, r2));
+        if (upper < lower) upper = lower;  // only reachable within rounding of a tangency
+    }
+    *tin = k.t_lo + lower;
+    *tout = k.t_lo + upper;
+}
+
+// Conservative FP32 filter, stage 1: the time extents overlap and the entry MBB meets the query
+// MBB expanded by d in every axis. Every bound is rounded outward (entry boxes at build time,
+// query boxes at query preparation), so a pair within distance d always passes.
+// ea = (xmin - d, ymin - d, zmin - d, w0) rounded down; eb = (xmax + d, ..., w1) rounded up.
+static __device__ __forceinline__ bool filter_box(const RecF &r, const float4 &ea, const float4 &eb)
+{
+    return (r.t0 < eb.w) & (r.t1 > ea.w) & (r.xmax >= ea.x) & (r.xmin <= eb.x) &
+           (r.ymax >= ea.y) & (r.ymin <= eb.y) & (r.zmax >= ea.z) & (r.zmin <= eb.z);
+}
+
+// Stage 2: the squared distance between the entry MBB and the query MBB with every subtraction,
+// product and sum rounded down (a lower bound of the squared separation over the window),
+// against an FP32 upper bound of d^2 that carries 1e-6 relative slack.
+// ua = (xmin, ymin, zmin, d2u) rounded down (d2u up); ub = (xmax, ymax, zmax, -) rounded up.
+static __device__ __forceinline__ bool filter_gap(const RecF &r, const float4 &ua, const float4 &ub)
+{
+    float gx = fmaxf(fmaxf(__fsub_rd(r.xmin, ub.x), __fsub_rd(ua.x, r.xmax)), 0.0f);
+    float gy = fmaxf(fmaxf(__fsub_rd(r.ymin, ub.y), __fsub_rd(ua.y, r.ymax)), 0.0f);
+    float gz = fmaxf(fmaxf(__fsub_rd(r.zmin, ub.z), __fsub_rd(ua.z, r.zmax)), 0.0f);
+    float s2 = __fmaf_rd(gz, gz, __fmaf_rd(gy, gy, __fmul_rd(gx, gx)));
+    return s2 <= ua.w;
+}
+
+}  // namespace ts

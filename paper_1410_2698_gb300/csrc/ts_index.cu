@@ -256,47 +256,20 @@ __global__ void k_gather_rec(const uint32_t *ids, uint64_t len, const RecF *rec,
     if (p < len) out[p] = rec[ids[p]];
 }
 
-// grid: per sorted entry the cell ranges in x, y, z; count = product; first cell packed
-__global__ void k_grid_count(const double *lo3, const double *hi3, uint64_t n, double gx, double gy,
-                             double gz, double wx, double wy, double wz, int g, uint32_t *cnt,
-                             uint32_t *cell0)
+// grid: every sorted entry is keyed by the cell of its MBB's minimum corner (single assignment)
+__global__ void k_grid_key(const double *lo3, uint64_t n, double gx, double gy, double gz,
+                           double wx, double wy, double wz, int g, uint32_t *keys, uint32_t *vals)
 {
     uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const double plo[3] = {gx, gy, gz}, pw[3] = {wx, wy, wz};
-    uint32_t c = 1, packed = 0;
+    uint32_t c[3];
     for (int d = 0; d < 3; d++) {
         int a = part_of(lo3[(uint64_t)d * n + s], plo[d], pw[d], g);
-        int b = part_of(hi3[(uint64_t)d * n + s], plo[d], pw[d], g);
-        if (a < 0) a = 0;
-        c *= b >= a ? (uint32_t)(b - a + 1) : 0u;
-        packed |= (uint32_t)a << (10 * d);
+        c[d] = (uint32_t)(a < 0 ? 0 : a);
     }
-    cnt[s] = c;
-    cell0[s] = packed;
-}
-
-__global__ void k_grid_emit(const double *lo3, const double *hi3, uint64_t n, double gx, double gy,
-                            double gz, double wx, double wy, double wz, int g,
-                            const uint32_t *pos, uint32_t *keys, uint32_t *vals)
-{
-    uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const double plo[3] = {gx, gy, gz}, pw[3] = {wx, wy, wz};
-    int a[3], b[3];
-    for (int d = 0; d < 3; d++) {
-        a[d] = part_of(lo3[(uint64_t)d * n + s], plo[d], pw[d], g);
-        b[d] = part_of(hi3[(uint64_t)d * n + s], plo[d], pw[d], g);
-        if (a[d] < 0) a[d] = 0;
-    }
-    uint32_t p = pos[s];
-    for (int cx = a[0]; cx <= b[0]; cx++)
-        for (int cy = a[1]; cy <= b[1]; cy++)
-            for (int cz = a[2]; cz <= b[2]; cz++) {
-                keys[p] = ((uint32_t)cx * g + cy) * g + cz;
-                vals[p] = (uint32_t)s;
-                p++;
-            }
+    keys[s] = (c[0] * (uint32_t)g + c[1]) * (uint32_t)g + c[2];
+    vals[s] = (uint32_t)s;
 }
 
 __global__ void k_hist_u32(const uint32_t *keys, uint64_t len, uint32_t *cnt)
@@ -388,37 +361,29 @@ ts_status build_st_dim(Ctx &c, Index *ix, int dim, const double *lo, const doubl
 
 ts_status build_grid(Ctx &c, Index *ix, const double *lo3, const double *hi3)
 {
+    (void)hi3;
     const uint64_t n = ix->n;
     const int g = (int)ix->g;
-    DevBuf cnt, pos;
-    TS_CHECK(cnt.alloc(sizeof(uint32_t) * n, c.s));
-    TS_CHECK(ix->alloc(&ix->g_cell0, n));
-    k_grid_count<<<nblocks(n), TPB, 0, c.s>>>(lo3, hi3, n, ix->g_lo[0], ix->g_lo[1], ix->g_lo[2],
-                                              ix->g_w[0], ix->g_w[1], ix->g_w[2], g,
-                                              cnt.as<uint32_t>(), ix->g_cell0);
-    TS_LAUNCHED();
-    uint64_t len = 0;
-    TS_CHECK(counts_to_pos(c, cnt.as<uint32_t>(), n, pos, &len));
     DevBuf keys;
-    TS_CHECK(keys.alloc(sizeof(uint32_t) * len, c.s));
-    TS_CHECK(ix->alloc(&ix->ga, len));
-    k_grid_emit<<<nblocks(n), TPB, 0, c.s>>>(lo3, hi3, n, ix->g_lo[0], ix->g_lo[1], ix->g_lo[2],
-                                             ix->g_w[0], ix->g_w[1], ix->g_w[2], g,
-                                             pos.as<uint32_t>(), keys.as<uint32_t>(), ix->ga);
+    TS_CHECK(keys.alloc(sizeof(uint32_t) * n, c.s));
+    TS_CHECK(ix->alloc(&ix->ga, n));
+    k_grid_key<<<nblocks(n), TPB, 0, c.s>>>(lo3, n, ix->g_lo[0], ix->g_lo[1], ix->g_lo[2],
+                                            ix->g_w[0], ix->g_w[1], ix->g_w[2], g,
+                                            keys.as<uint32_t>(), ix->ga);
     TS_LAUNCHED();
-    uint64_t ncell = (uint64_t)g * g * g;
-    TS_CHECK(radix_sort_u32(keys.as<uint32_t>(), ix->ga, len, bits_for(ncell - 1), c.s));
+    const uint64_t ncell = (uint64_t)g * g * g;
+    TS_CHECK(radix_sort_u32(keys.as<uint32_t>(), ix->ga, n, bits_for(ncell - 1), c.s));
     DevBuf h;
     TS_CHECK(h.alloc(sizeof(uint32_t) * ncell, c.s));
     TS_CUDA(cudaMemsetAsync(h.p, 0, sizeof(uint32_t) * ncell, c.s));
-    k_hist_u32<<<nblocks(len), TPB, 0, c.s>>>(keys.as<uint32_t>(), len, h.as<uint32_t>());
+    k_hist_u32<<<nblocks(n), TPB, 0, c.s>>>(keys.as<uint32_t>(), n, h.as<uint32_t>());
     TS_LAUNCHED();
     TS_CHECK(ix->alloc(&ix->g_off, ncell + 1));
     TS_CHECK(scan_u32(h.as<uint32_t>(), ix->g_off, ncell, c.status.as<uint32_t>(), c.s));
-    TS_CHECK(ix->alloc(&ix->ga_rec, len));
-    k_gather_rec<<<nblocks(len), TPB, 0, c.s>>>(ix->ga, len, ix->rec, ix->ga_rec);
+    TS_CHECK(ix->alloc(&ix->ga_rec, n));
+    k_gather_rec<<<nblocks(n), TPB, 0, c.s>>>(ix->ga, n, ix->rec, ix->ga_rec);
     TS_LAUNCHED();
-    ix->g_len = len;
+    ix->g_len = n;
     return c.read_status();
 }
 

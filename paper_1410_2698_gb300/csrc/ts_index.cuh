@@ -40,14 +40,14 @@ struct Index {
     uint32_t *st_off[3] = {nullptr, nullptr, nullptr};
     uint64_t st_len[3] = {0, 0, 0};
 
-    // flatly structured grid (Sec. 4.1): dense cell offsets over g^3 cells, lookup array A with a
-    // duplicated prefilter record per entry, and each entry's first cell (packed 3 x 10 bits)
+    // flatly structured grid (Sec. 4.1), one cell per entry (the cell of its MBB's minimum
+    // corner): dense cell offsets over g^3 cells and the lookup array A with a copy of each
+    // entry's prefilter record
     uint32_t g = 0;
     double g_lo[3] = {0, 0, 0}, g_w[3] = {0, 0, 0};
     uint32_t *ga = nullptr;
     RecF *ga_rec = nullptr;
     uint32_t *g_off = nullptr;  // g^3 + 1
-    uint32_t *g_cell0 = nullptr;  // per sorted entry
     uint64_t g_len = 0;
 
     size_t bytes = 0;

@@ -1,27 +1,35 @@
-// ts_search.cu -- the search: query preparation, candidate schedule, query grouping, and the pair
-// kernel with its count -> scan -> write result path.
+// ts_search.cu -- the search pipeline: query preparation and schedule, candidate units, groups,
+// and the pair kernel with its count -> scan -> write result path.
 //
 // Paper mapping (Gowanlock & Casanova):
-//   query preparation + schedule : the host-side schedule S of Sec. 4.2 and Sec. 4.3, here one
-//                                  device thread per query segment (binary searches on the bin
-//                                  prefix maximum replace the carried scan)
-//   pair kernel                  : the compare() loop of Alg. 1-3; one warp sweeps the candidate
-//                                  range of up to 32 queries (one per lane) instead of one thread
-//                                  per query; results are counted, scanned and written at fixed
-//                                  offsets instead of atomically appended to a fixed buffer.
+//   query preparation + schedule : the host-side schedule S of Sec. 4.2 and Sec. 4.3 and the
+//                                  cell lookup of Sec. 4.1, here one device thread per query
+//                                  segment (binary searches on the bins' prefix maximum replace
+//                                  the carried scan; a dense cell offset array replaces the
+//                                  binary search in G)
+//   pair kernel                  : the compare() loop of Alg. 1-3. A warp takes a tile of up to
+//                                  PK_TILE consecutive candidate records shared by a group of up
+//                                  to 32 candidate ranges; each lane holds one record and the
+//                                  warp loops over the group's members, so a record is fetched
+//                                  once for up to 32 query segments. Results are counted,
+//                                  scanned and written at fixed offsets instead of being appended
+//                                  atomically to a fixed-size buffer.
 //
-// The pair test has two stages:
-//   1. a conservative FP32 filter: time extents and MBBs rounded outward to FP32 (directed
-//      rounding), the squared box distance accumulated rounding down; a pair is dropped only
-//      when the lower bound of its separation exceeds d (with 1e-6 relative slack), so no pair
-//      the FP64 test could accept is ever dropped;
-//   2. the exact FP64 test on the survivors (the closed form of the interaction, evaluated
-//      without FMA contraction so it reproduces the plain definition's rounding), compacted
-//      32 at a time with ballot/popc so the FP64 pipe runs full warps.
+// The pair test has three stages:
+//   1. FP32 box test: time extents and the entry MBB against the query MBB expanded by d, all
+//      bounds rounded outward (8 compares);
+//   2. FP32 gap test: squared MBB distance accumulated rounding down against an upper bound of
+//      d^2 (run only when some lane passed stage 1); a pair is dropped only when a lower bound
+//      of its separation exceeds d, so no pair the FP64 test could accept is ever dropped;
+//   3. the exact FP64 test on the survivors (the closed form of the interaction, evaluated
+//      without FMA contraction so it reproduces the plain definition's rounding), run 32 at a
+//      time on survivors compacted with ballot/popc so the FP64 pipe runs full warps.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
+#include "ts_device.cuh"
 #include "ts_search.cuh"
 
 namespace ts {
@@ -29,181 +37,29 @@ namespace ts {
 namespace {
 
 constexpr int TPB = 256;
-inline unsigned nblk(uint64_t n) { return (unsigned)((n + TPB - 1) / TPB ? (n + TPB - 1) / TPB : 1); }
-
-// ---------------------------------------------------------------------------------------------
-// PTX wrappers: mbarrier + 1-D bulk copy (TMA engine), globaltimer
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
+inline unsigned nblk(uint64_t n)
 {
-    return (uint32_t)__cvta_generic_to_shared(p);
+    uint64_t b = (n + TPB - 1) / TPB;
+    if (b == 0) b = 1;
+    if (b > 65535u * 32u) b = 65535u * 32u;
+    return (unsigned)b;
 }
 
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
+// Relative slack added to the d-expanded query extents before they are mapped to subbins or grid
+// cells, so FP64 rounding of (min - d) can never exclude a cell that holds a pair within d.
+constexpr double EXT_SLACK = 1e-12;
 
-__device__ __forceinline__ void fence_mbar_init()
+__device__ __forceinline__ uint32_t req_of(const ReqDesc *reqs, uint32_t nreq, uint32_t i)
 {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
-                                         unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t globaltimer_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait on an mbarrier phase: gives up after ~2 s of wall time.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0 && globaltimer_ns() - t0 > 2000000000ull) return false;
+    uint32_t lo = 0, hi = nreq;  // last r with q_first <= i
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) / 2;
+        if (reqs[mid].q_first <= i) lo = mid; else hi = mid;
     }
+    return lo;
 }
 
-// ---------------------------------------------------------------------------------------------
-// exact FP64 interaction test (same operation order as the plain definition; no contraction)
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ double dmx(double a, double b) { return a > b ? a : b; }
-__device__ __forceinline__ double dmn(double a, double b) { return a < b ? a : b; }
-
-struct Quad {
-    double t_lo, T, a, b, c;
-};
-
-// Window and quadratic coefficients; false when the common window has no positive length.
-__device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e, double dd, Quad &o)
-{
-    double t_lo = dmx(q.w0, e.t0);
-    double t_hi = dmn(q.w1, e.t1);
-    if (!(t_lo < t_hi)) return false;
-    double dq = t_lo - q.t0, de = t_lo - e.t0;
-    double rx = (q.x0 + q.vx * dq) - (e.x0 + e.vx * de);
-    double ry = (q.y0 + q.vy * dq) - (e.y0 + e.vy * de);
-    double rz = (q.z0 + q.vz * dq) - (e.z0 + e.vz * de);
-    double dvx = q.vx - e.vx, dvy = q.vy - e.vy, dvz = q.vz - e.vz;
-    o.t_lo = t_lo;
-    o.T = t_hi - t_lo;
-    o.a = (dvx * dvx + dvy * dvy) + dvz * dvz;
-    o.b = (rx * dvx + ry * dvy) + rz * dvz;
-    o.c = ((rx * rx + ry * ry) + rz * rz) - dd;
-    return true;
-}
-
-// Division-free hit decision: the minimum of a tau^2 + 2 b tau + c over [0, T] is <= 0.
-__device__ __forceinline__ bool quad_hit(const Quad &k)
-{
-    if (k.a == 0.0) return k.c <= 0.0;
-    if (k.b >= 0.0) return k.c <= 0.0;                       // minimum at tau = 0
-    if (-k.b >= k.a * k.T) return (k.a * k.T + 2.0 * k.b) * k.T + k.c <= 0.0;  // at tau = T
-    return k.b * k.b - k.a * k.c >= 0.0;                     // interior minimum
-}
-
-// Interval of a hit from the numerically stable root pair s/a, c/s.
-__device__ __forceinline__ void quad_interval(const Quad &k, double *tin, double *tout)
-{
-    double lower, upper;
-    if (k.a == 0.0) {
-        lower = 0.0;
-        upper = k.T;
-    } else {
-        double disc = k.b * k.b - k.a * k.c;
-        if (disc < 0.0) disc = 0.0;  // only reachable within rounding of a tangency
-        double sq = sqrt(disc);
-        double s = -(k.b + copysign(sq, k.b));
-        double r1, r2;
-        if (s == 0.0) {
-            r1 = 0.0;
-            r2 = 0.0;
-        } else {
-            r1 = s / k.a;
-            r2 = k.c / s;
-        }
-        lower = dmx(0.0, dmn(r1, r2));
-        upper = dmn(k.T, dmx(r1, r2));
-        if (upper < lower) upper = lower;  // only reachable within rounding of a tangency
-    }
-    *tin = k.t_lo + lower;
-    *tout = k.t_lo + upper;
-}
-
-// Conservative FP32 filter (see file header).
-__device__ __forceinline__ bool prefilter(const RecF &r, const float4 &qa, const float4 &qb,
-                                          float d2u)
-{
-    bool t = (r.t0 < qb.w) && (r.t1 > qa.w);
-    float gx = fmaxf(fmaxf(__fsub_rd(r.xmin, qb.x), __fsub_rd(qa.x, r.xmax)), 0.0f);
-    float gy = fmaxf(fmaxf(__fsub_rd(r.ymin, qb.y), __fsub_rd(qa.y, r.ymax)), 0.0f);
-    float gz = fmaxf(fmaxf(__fsub_rd(r.zmin, qb.z), __fsub_rd(qa.z, r.zmax)), 0.0f);
-    float s2 = __fmaf_rd(gz, gz, __fmaf_rd(gy, gy, __fmul_rd(gx, gx)));
-    return t && (s2 <= d2u);
-}
-
-// ---------------------------------------------------------------------------------------------
-// query preparation and schedule (one thread per caller query)
-// ---------------------------------------------------------------------------------------------
-struct PrepParams {
-    const double *f[8];
-    uint64_t nq;
-    int kind;
-    double d, Ts, Te;
-    // index
-    uint64_t n;
-    uint32_t m;
-    double tmin, tmax;
-    const double *bin_start, *bin_pmax;
-    const uint32_t *bin_off;
-    uint32_t v[3];
-    double sub_lo[3], sub_w[3];
-    const uint32_t *st_off[3];
-    // outputs
-    QueryD *qd;
-    float4 *qf;
-    uint32_t *qlo, *qhi, *qsel;
-    uint64_t *keys;
-    uint32_t *vals;
-    unsigned long long *stats;
-    uint32_t *status;
-};
-
-__device__ inline uint32_t first_pmax_above(const double *pmax, uint32_t m, double w0)
+__device__ __forceinline__ uint32_t first_pmax_above(const double *pmax, uint32_t m, double w0)
 {
     uint32_t lo = 0, hi = m;
     while (lo < hi) {
@@ -214,9 +70,9 @@ __device__ inline uint32_t first_pmax_above(const double *pmax, uint32_t m, doub
 }
 
 // last bin with start < w1, or -1
-__device__ inline int last_start_below(const double *bs, uint32_t m, double w1)
+__device__ __forceinline__ int last_start_below(const double *bs, uint32_t m, double w1)
 {
-    uint32_t lo = 0, hi = m;  // first j with bs[j] >= w1
+    uint32_t lo = 0, hi = m;
     while (lo < hi) {
         uint32_t mid = lo + (hi - lo) / 2;
         if (bs[mid] >= w1) hi = mid; else lo = mid + 1;
@@ -224,12 +80,41 @@ __device__ inline int last_start_below(const double *bs, uint32_t m, double w1)
     return (int)lo - 1;
 }
 
+// ---------------------------------------------------------------------------------------------
+// query preparation (one thread per query segment of the batch)
+// ---------------------------------------------------------------------------------------------
+struct PrepParams {
+    const double *f[8];
+    uint64_t nq;
+    int kind;
+    const ReqDesc *reqs;
+    uint32_t nreq;
+    int lo_bits;
+    // index
+    uint64_t n;
+    uint32_t m;
+    double tmin, tmax;
+    const double *bin_start, *bin_pmax;
+    const uint32_t *bin_off;
+    uint32_t v[3];
+    double sub_lo[3], sub_w[3];
+    const uint32_t *st_off[3];
+    uint32_t g;
+    double g_lo[3], g_w[3], longest[3];
+    PipeBufs b;
+};
+
+__device__ __forceinline__ uint64_t unit_key(uint32_t r, uint32_t sel, uint32_t lo, int lo_bits)
+{
+    return ((uint64_t)r << (3 + lo_bits)) | ((uint64_t)sel << lo_bits) | (uint64_t)lo;
+}
+
 __global__ void k_qprep(PrepParams P)
 {
-    uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool in = i < P.nq;
-    bool valid = false, subbin = false;
-    if (in) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.nq;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = req_of(P.reqs, P.nreq, (uint32_t)i);
+        const ReqDesc R = P.reqs[r];
         double v[8];
         bool fin = true;
 #pragma unroll
@@ -237,172 +122,236 @@ __global__ void k_qprep(PrepParams P)
             v[k] = P.f[k][i];
             fin = fin && isfinite(v[k]);
         }
-        if (!fin || !(v[7] > v[3])) atomicOr(P.status, DEV_ERR_INVALID);
-        double dt = v[7] - v[3];
+        if (!fin || !(v[7] > v[3])) atomicOr(P.b.status, DEV_ERR_INVALID);
+        const double dt = v[7] - v[3];
         QueryD q;
         q.x0 = v[0]; q.y0 = v[1]; q.z0 = v[2]; q.t0 = v[3];
         q.vx = (v[4] - v[0]) / dt;
         q.vy = (v[5] - v[1]) / dt;
         q.vz = (v[6] - v[2]) / dt;
-        q.w0 = dmx(v[3], P.Ts);
-        q.w1 = dmn(v[7], P.Te);
-        q.pad = 0.0;
-        valid = fin && (v[7] > v[3]) && (q.w0 < q.w1);
-        P.qd[i] = q;
+        q.w0 = dmx(v[3], R.t_start);
+        q.w1 = dmn(v[7], R.t_end);
+        q.pad = R.dd;
+        const bool valid = fin && (v[7] > v[3]) && (q.w0 < q.w1);
+        P.b.qd[i] = q;
+        P.b.qreq[i] = r;
         double mn[3], mx[3];
+        float fmn[3], fmx[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             mn[d] = v[d] < v[4 + d] ? v[d] : v[4 + d];
             mx[d] = v[d] < v[4 + d] ? v[4 + d] : v[d];
+            fmn[d] = __double2float_rd(mn[d]);
+            fmx[d] = __double2float_ru(mx[d]);
         }
-        P.qf[2 * i] = make_float4(__double2float_rd(mn[0]), __double2float_rd(mn[1]),
-                                  __double2float_rd(mn[2]), __double2float_rd(q.w0));
-        P.qf[2 * i + 1] = make_float4(__double2float_ru(mx[0]), __double2float_ru(mx[1]),
-                                      __double2float_ru(mx[2]), __double2float_ru(q.w1));
-        uint32_t sel = SEL_T, lo = 0, hi = 0, j = 0;
-        if (valid) {
-            if (P.kind == TS_INDEX_BRUTE) {
-                lo = 0;
-                hi = (uint32_t)P.n;
-            } else {
-                // temporal range (Sec. 4.2 schedule)
-                uint32_t jl = first_pmax_above(P.bin_pmax, P.m, q.w0);
-                int jh = last_start_below(P.bin_start, P.m, q.w1);
-                bool any = (int)jl <= jh;
-                if (any) {
-                    lo = P.bin_off[jl];
-                    hi = P.bin_off[jh + 1];
-                }
-                if (any && P.kind == TS_INDEX_SPATIOTEMPORAL) {
-                    // dimension whose d-expanded extent meets one subbin (or none) with the
-                    // fewest ids over the bins jl..jh (Sec. 4.3 schedule)
-                    long long best = -1;
+        P.b.qf[4 * i + 0] = make_float4(__fsub_rd(fmn[0], R.d_up), __fsub_rd(fmn[1], R.d_up),
+                                        __fsub_rd(fmn[2], R.d_up), __double2float_rd(q.w0));
+        P.b.qf[4 * i + 1] = make_float4(__fadd_ru(fmx[0], R.d_up), __fadd_ru(fmx[1], R.d_up),
+                                        __fadd_ru(fmx[2], R.d_up), __double2float_ru(q.w1));
+        P.b.qf[4 * i + 2] = make_float4(fmn[0], fmn[1], fmn[2], R.d2u);
+        P.b.qf[4 * i + 3] = make_float4(fmx[0], fmx[1], fmx[2], 0.0f);
+
+        uint32_t sel = SEL_T, lo = 0, hi = 0;
+        bool subbin = false;
+        if (P.kind == TS_INDEX_SPATIAL) {
+            // cells of the grid (single assignment by MBB minimum corner) that can hold an entry
+            // within d: minimum corners in [min - d - longest, max + d] per axis
+            uint32_t ca[3], cb[3];
+            bool any = valid;
 #pragma unroll
-                    for (int d = 0; d < 3; d++) {
-                        int vv = (int)P.v[d];
-                        int pa = part_of(mn[d] - P.d, P.sub_lo[d], P.sub_w[d], vv);
-                        int pb = part_of(mx[d] + P.d, P.sub_lo[d], P.sub_w[d], vv);
-                        int ja = pa < 0 ? 0 : pa, jb = pb;
-                        uint32_t clo, chi;
-                        if (jb < ja) {
-                            clo = 0;
-                            chi = 0;
-                        } else if (ja == jb) {
-                            const uint32_t *off = P.st_off[d];
-                            clo = off[(uint64_t)ja * P.m + jl];
-                            chi = off[(uint64_t)ja * P.m + jh + 1];
-                        } else {
-                            continue;
-                        }
-                        if (best < 0 || (long long)(chi - clo) < best) {
-                            best = (long long)(chi - clo);
-                            sel = (uint32_t)d;
-                            lo = clo;
-                            hi = chi;
-                            j = jb < ja ? 0u : (uint32_t)ja;
-                        }
+            for (int d = 0; d < 3; d++) {
+                double a = ((mn[d] - R.d) - P.longest[d]) -
+                           EXT_SLACK * ((fabs(mn[d]) + R.d) + P.longest[d]);
+                double bb = (mx[d] + R.d) + EXT_SLACK * (fabs(mx[d]) + R.d);
+                int pa = part_of(a, P.g_lo[d], P.g_w[d], (int)P.g);
+                int pb = part_of(bb, P.g_lo[d], P.g_w[d], (int)P.g);
+                if (pa < 0) pa = 0;
+                if (pb < pa) any = false;
+                ca[d] = (uint32_t)pa;
+                cb[d] = (uint32_t)(pb < 0 ? 0 : pb);
+            }
+            P.b.qcell[2 * i] = ca[0] | (ca[1] << 10) | (ca[2] << 20);
+            P.b.qcell[2 * i + 1] = cb[0] | (cb[1] << 10) | (cb[2] << 20);
+            P.b.qnu[i] = any ? (cb[0] - ca[0] + 1) * (cb[1] - ca[1] + 1) : 0u;
+        } else {
+            if (valid) {
+                if (P.kind == TS_INDEX_BRUTE) {
+                    hi = (uint32_t)P.n;
+                } else {
+                    // temporal range (Sec. 4.2 schedule)
+                    const uint32_t jl = first_pmax_above(P.bin_pmax, P.m, q.w0);
+                    const int jh = last_start_below(P.bin_start, P.m, q.w1);
+                    const bool any = (int)jl <= jh;
+                    if (any) {
+                        lo = P.bin_off[jl];
+                        hi = P.bin_off[jh + 1];
                     }
-                    subbin = best >= 0;
+                    if (any && P.kind == TS_INDEX_SPATIOTEMPORAL) {
+                        // the dimension whose d-expanded extent meets one subbin (or none) with
+                        // the fewest ids over the bins jl..jh (Sec. 4.3 schedule)
+                        long long best = -1;
+#pragma unroll
+                        for (int d = 0; d < 3; d++) {
+                            const int vv = (int)P.v[d];
+                            double a = (mn[d] - R.d) - EXT_SLACK * (fabs(mn[d]) + R.d);
+                            double bb = (mx[d] + R.d) + EXT_SLACK * (fabs(mx[d]) + R.d);
+                            const int pa = part_of(a, P.sub_lo[d], P.sub_w[d], vv);
+                            const int pb = part_of(bb, P.sub_lo[d], P.sub_w[d], vv);
+                            const int ja = pa < 0 ? 0 : pa, jb = pb;
+                            uint32_t clo, chi;
+                            if (jb < ja) {
+                                clo = 0;
+                                chi = 0;
+                            } else if (ja == jb) {
+                                const uint32_t *off = P.st_off[d];
+                                clo = off[(uint64_t)ja * P.m + jl];
+                                chi = off[(uint64_t)ja * P.m + jh + 1];
+                            } else {
+                                continue;
+                            }
+                            if (best < 0 || (long long)(chi - clo) < best) {
+                                best = (long long)(chi - clo);
+                                sel = (uint32_t)d;
+                                lo = clo;
+                                hi = chi;
+                            }
+                        }
+                        subbin = best >= 0;
+                    }
                 }
             }
+            const bool unit = valid && hi > lo;
+            P.b.u_q[i] = (uint32_t)i;
+            P.b.u_lo[i] = lo;
+            P.b.u_hi[i] = hi;
+            P.b.u_sel[i] = sel;
+            P.b.keys[i] = unit ? unit_key(r, sel, lo, P.lo_bits) : ~0ull;
+            P.b.vals[i] = (uint32_t)i;
+            if (unit) atomicAdd(&P.b.req_units[r], 1u);
         }
-        P.qlo[i] = lo;
-        P.qhi[i] = hi;
-        P.qsel[i] = sel;
-        uint64_t key = ~0ull;
-        if (valid) {
-            double span = P.tmax - P.tmin;
-            double u = span > 0.0 ? (q.w0 - P.tmin) / span : 0.0;
-            u = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
-            uint32_t qt = (uint32_t)(u * 4294967295.0);
-            uint32_t gk = (sel << 28) | (j & 0x0fffffffu);
-            key = ((uint64_t)gk << 32) | qt;
+        const unsigned am = __activemask();
+        const unsigned vm = __ballot_sync(am, valid);
+        const unsigned sm = __ballot_sync(am, subbin);
+        const int lane = threadIdx.x & 31;
+        if (lane == __ffs(am) - 1) {
+            if (vm) atomicAdd(&P.b.stats[ST_QSEGS], (unsigned long long)__popc(vm));
+            if (sm) atomicAdd(&P.b.stats[ST_SUBBIN], (unsigned long long)__popc(sm));
         }
-        P.keys[i] = key;
-        P.vals[i] = (uint32_t)i;
     }
-    unsigned vm = __ballot_sync(0xffffffffu, valid);
-    unsigned sm = __ballot_sync(0xffffffffu, subbin);
-    if ((threadIdx.x & 31) == 0) {
-        if (vm) atomicAdd(&P.stats[ST_QSEGS], (unsigned long long)__popc(vm));
-        if (sm) atomicAdd(&P.stats[ST_SUBBIN], (unsigned long long)__popc(sm));
+}
+
+// Grid index: one unit per (cx, cy) of a query's cell box, covering cells cz_a..cz_b (a z-run
+// of the row-major cell order, contiguous in the lookup array).
+__global__ void k_grid_units(uint64_t nq, int lo_bits, uint32_t g, const uint32_t *g_off,
+                             PipeBufs b)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t nu = b.qnu[i];
+        if (!nu) continue;
+        const uint32_t r = b.qreq[i];
+        const uint32_t w0 = b.qcell[2 * i], w1 = b.qcell[2 * i + 1];
+        const uint32_t ax = w0 & 1023u, ay = (w0 >> 10) & 1023u, az = (w0 >> 20) & 1023u;
+        const uint32_t bx = w1 & 1023u, by = (w1 >> 10) & 1023u, bz = (w1 >> 20) & 1023u;
+        uint32_t u = b.quoff[i];
+        uint32_t nvalid = 0;
+        for (uint32_t cx = ax; cx <= bx; cx++)
+            for (uint32_t cy = ay; cy <= by; cy++, u++) {
+                const uint64_t row = ((uint64_t)cx * g + cy) * g;
+                const uint32_t lo = g_off[row + az], hi = g_off[row + bz + 1];
+                b.u_q[u] = (uint32_t)i;
+                b.u_lo[u] = lo;
+                b.u_hi[u] = hi;
+                b.u_sel[u] = SEL_GRID;
+                b.keys[u] = hi > lo ? unit_key(r, SEL_GRID, lo, lo_bits) : ~0ull;
+                b.vals[u] = u;
+                nvalid += hi > lo;
+            }
+        if (nvalid) atomicAdd(&b.req_units[r], nvalid);
     }
 }
 
 // ---------------------------------------------------------------------------------------------
-// grouping: runs of equal group key in sorted order, cut into groups of <= 32 queries
+// groups
 // ---------------------------------------------------------------------------------------------
-__device__ inline uint32_t gk_of(uint64_t key) { return (uint32_t)(key >> 32); }
-
-__global__ void k_group_mark(const uint64_t *keys, uint64_t nq, const unsigned long long *stats,
-                             uint32_t *flags)
+// Per request: unit starts (exclusive scan of its unit count) and group starts (ceil(units/32)).
+__global__ void k_req_scan(uint32_t nreq, PipeBufs b)
 {
-    uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nq) return;
-    uint64_t nvalid = stats[ST_QSEGS];
-    if (p >= nvalid) {
-        flags[p] = 0;
-        return;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint32_t us = 0, gs = 0;
+    for (uint32_t r = 0; r < nreq; r++) {
+        b.ustart[r] = us;
+        b.gstart[r] = gs;
+        const uint32_t n = b.req_units[r];
+        const uint32_t ng = (n + GROUP - 1) / GROUP;
+        b.req_groups[r] = ng;
+        us += n;
+        gs += ng;
     }
-    uint32_t gk = gk_of(keys[p]);
-    uint64_t lo = 0, hi = p;  // first position of this run
-    while (lo < hi) {
-        uint64_t mid = lo + (hi - lo) / 2;
-        if (gk_of(keys[mid]) < gk) lo = mid + 1; else hi = mid;
-    }
-    flags[p] = ((p - lo) % 32u) == 0 ? 1u : 0u;
+    b.ustart[nreq] = us;
+    b.gstart[nreq] = gs;
+    b.hdr[HDR_U] = us;
+    b.hdr[HDR_G] = gs;
 }
 
-__global__ void k_group_fill(const uint64_t *keys, const uint32_t *vals, uint64_t nq,
-                             const unsigned long long *stats, const uint32_t *flags,
-                             const uint32_t *gid, const uint32_t *qlo, const uint32_t *qhi,
-                             Group *groups, uint32_t *ntiles)
+__global__ void k_groups(uint32_t nreq, uint64_t gcap, PipeBufs b)
 {
-    uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nq || !flags[p]) return;
-    uint64_t nvalid = stats[ST_QSEGS];
-    uint32_t gk = gk_of(keys[p]);
-    uint64_t lo = p, hi = nvalid;  // end of this run
-    while (lo < hi) {
-        uint64_t mid = lo + (hi - lo) / 2;
-        if (gk_of(keys[mid]) <= gk) lo = mid + 1; else hi = mid;
-    }
-    uint32_t cnt = (uint32_t)((lo - p) < 32 ? (lo - p) : 32);
-    uint32_t ulo = 0xffffffffu, uhi = 0;
-    for (uint32_t k = 0; k < cnt; k++) {
-        uint32_t ci = vals[p + k];
-        if (qhi[ci] > qlo[ci]) {
-            ulo = min(ulo, qlo[ci]);
-            uhi = max(uhi, qhi[ci]);
+    const uint32_t G = b.hdr[HDR_G];
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < gcap;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        if (g >= G) {
+            b.ntiles[g] = 0;
+            continue;
         }
+        uint32_t lo = 0, hi = nreq;  // last r with gstart[r] <= g
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) / 2;
+            if (b.gstart[mid] <= g) lo = mid; else hi = mid;
+        }
+        const uint32_t r = lo;
+        const uint32_t first = b.ustart[r] + GROUP * ((uint32_t)g - b.gstart[r]);
+        const uint32_t end = min(first + GROUP, b.ustart[r] + b.req_units[r]);
+        b.g_first[g] = first;
+        b.g_count[g] = end - first;
+        // merge the members' ranges (sorted by array, then start) into disjoint segments
+        uint32_t nseg = 0, tiles = 0;
+        uint32_t cs = 0, clo = 0, chi = 0;
+        bool open = false;
+        uint32_t *slo = b.seg_lo + (uint64_t)g * GROUP, *shi = b.seg_hi + (uint64_t)g * GROUP;
+        uint32_t *ssel = b.seg_sel + (uint64_t)g * GROUP, *st0 = b.seg_t0 + (uint64_t)g * GROUP;
+        for (uint32_t p = first; p < end; p++) {
+            const uint32_t u = b.vals[p];
+            const uint32_t s = b.u_sel[u], ul = b.u_lo[u], uh = b.u_hi[u];
+            if (open && s == cs && ul <= chi) {
+                chi = max(chi, uh);
+                continue;
+            }
+            if (open) {
+                slo[nseg] = clo; shi[nseg] = chi; ssel[nseg] = cs; st0[nseg] = tiles;
+                tiles += (chi - clo + PK_TILE - 1) / PK_TILE;
+                nseg++;
+            }
+            open = true;
+            cs = s; clo = ul; chi = uh;
+        }
+        if (open) {
+            slo[nseg] = clo; shi[nseg] = chi; ssel[nseg] = cs; st0[nseg] = tiles;
+            tiles += (chi - clo + PK_TILE - 1) / PK_TILE;
+            nseg++;
+        }
+        b.g_nseg[g] = nseg;
+        b.ntiles[g] = tiles;
     }
-    if (uhi <= ulo) {
-        ulo = 0;
-        uhi = 0;
-    }
-    Group g;
-    g.first = (uint32_t)p;
-    g.count = cnt;
-    g.sel = gk >> 28;
-    g.lo = ulo;
-    g.hi = uhi;
-    g.pad[0] = g.pad[1] = g.pad[2] = 0;
-    uint32_t id = gid[p];
-    groups[id] = g;
-    ntiles[id] = (uhi - ulo + PK_TILE - 1) / PK_TILE;
 }
 
-__global__ void k_hdr(const unsigned long long *stats_in, const uint32_t *gid, const uint64_t *tile_base,
-                      uint64_t nq, uint32_t *hdr, unsigned long long *stats)
+__global__ void k_hdr(uint64_t gcap, uint64_t tcap, PipeBufs b)
 {
-    uint32_t ng = gid[nq];
-    uint64_t nt = tile_base[nq];
-    hdr[HDR_NVALID] = (uint32_t)stats_in[ST_QSEGS];
-    hdr[HDR_NGROUPS] = ng;
-    hdr[HDR_NTILES_LO] = (uint32_t)nt;
-    hdr[HDR_NTILES_HI] = (uint32_t)(nt >> 32);
-    stats[ST_GROUPS] = ng;
-    stats[ST_TILES] = nt;
+    const uint64_t T = b.tile_base[gcap];
+    b.hdr[HDR_T_LO] = (uint32_t)T;
+    b.hdr[HDR_T_HI] = (uint32_t)(T >> 32);
+    b.stats[ST_GROUPS] = b.hdr[HDR_G];
+    b.stats[ST_TILES] = T;
+    if (T > tcap) atomicOr(b.status, DEV_ERR_OVERFLOW);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -410,14 +359,25 @@ __global__ void k_hdr(const unsigned long long *stats_in, const uint32_t *gid, c
 // ---------------------------------------------------------------------------------------------
 struct __align__(16) WarpSmem {
     RecF stage[2][PK_CH];
-    QueryD qd[32];
-    uint32_t qorig[32];
+    float4 ea[GROUP], eb[GROUP], ua[GROUP], ub[GROUP];
+    uint2 rng[GROUP];
+    uint32_t qg[GROUP];   // query index in the batch
+    uint32_t ql[GROUP];   // query index within its request
     uint32_t queue[64];
     unsigned long long bar[2];
-    uint32_t pad[2];
 };
 
 enum { PASS_COUNT = 0, PASS_WRITE = 1 };
+
+struct PairParams {
+    PipeBufs b;
+    const ReqDesc *reqs;
+    const RecF *rec[5];
+    const uint32_t *ids[5];
+    const SegD *seg;
+    const uint32_t *orig;
+    uint64_t tcap;
+};
 
 __device__ __forceinline__ uint32_t find_group(const uint64_t *base, uint32_t ng, uint64_t t)
 {
@@ -438,6 +398,7 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pair(PairParams P)
     WarpSmem &W = reinterpret_cast<WarpSmem *>(smem_raw)[wid];
     const unsigned FULL = 0xffffffffu;
     const uint32_t lt_mask = (1u << lane) - 1u;
+    const PipeBufs &B = P.b;
 
     if (lane == 0) {
         mbar_init(&W.bar[0], 1);
@@ -449,120 +410,137 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pair(PairParams P)
     bool pending[2] = {false, false};
     bool abort = false;
 
-    const uint32_t ngroups = P.hdr[HDR_NGROUPS];
-    const uint64_t ntiles = (uint64_t)P.hdr[HDR_NTILES_LO] | ((uint64_t)P.hdr[HDR_NTILES_HI] << 32);
+    const uint32_t ngroups = B.hdr[HDR_G];
+    uint64_t ntiles = (uint64_t)B.hdr[HDR_T_LO] | ((uint64_t)B.hdr[HDR_T_HI] << 32);
+    if (ntiles > P.tcap) ntiles = 0;  // overflow already flagged
     unsigned long long acc_tests = 0, acc_exact = 0, acc_hits = 0;
 
     while (!abort) {
         uint64_t t = 0;
-        if (lane == 0) t = atomicAdd(P.tile_counter, 1u);
+        if (lane == 0) t = atomicAdd(&B.counters[PASS], 1u);
         t = __shfl_sync(FULL, t, 0);
         if (t >= ntiles) break;
-        const uint32_t g = find_group(P.tile_base, ngroups, t);
-        const Group G = P.groups[g];
-        const uint32_t s0 = G.lo + (uint32_t)(t - P.tile_base[g]) * PK_TILE;
-        const uint32_t s1 = min(G.hi, s0 + PK_TILE);
-        const RecF *recs = P.rec[G.sel];
-        const uint32_t *ids = P.ids[G.sel];
+        const uint32_t g = find_group(B.tile_base, ngroups, t);
+        const uint32_t lt = (uint32_t)(t - B.tile_base[g]);
+        const uint32_t nseg = B.g_nseg[g];
+        const uint32_t *st0 = B.seg_t0 + (uint64_t)g * GROUP;
+        uint32_t k = 0;
+        while (k + 1 < nseg && st0[k + 1] <= lt) k++;
+        const uint32_t sel = B.seg_sel[(uint64_t)g * GROUP + k];
+        const uint32_t s0 = B.seg_lo[(uint64_t)g * GROUP + k] + (lt - st0[k]) * PK_TILE;
+        const uint32_t s1 = min(B.seg_hi[(uint64_t)g * GROUP + k], s0 + PK_TILE);
+        const uint32_t first = B.g_first[g], count = B.g_count[g];
+        const RecF *recs = P.rec[sel];
+        const uint32_t *ids = P.ids[sel];
 
-        // this lane's query
-        const bool act = (uint32_t)lane < G.count;
-        float4 qa = make_float4(0.f, 0.f, 0.f, 0.f), qb = qa;
-        uint32_t qlo = 0, qhi = 0;
-        if (act) {
-            uint32_t ci = P.qval[G.first + lane];
-            qa = P.qf[2 * (uint64_t)ci];
-            qb = P.qf[2 * (uint64_t)ci + 1];
-            qlo = P.qlo[ci];
-            qhi = P.qhi[ci];
-            W.qd[lane] = P.qd[ci];
-            W.qorig[lane] = ci;
-        }
-        if (PASS == PASS_COUNT) {
-            uint32_t a = max(qlo, s0), b = min(qhi, s1);
-            acc_tests += (act && b > a) ? (b - a) : 0u;
+        // members of the group (one per lane)
+        if ((uint32_t)lane < count) {
+            const uint32_t u = B.vals[first + lane];
+            const uint32_t qi = B.u_q[u];
+            uint32_t lo = B.u_lo[u], hi = B.u_hi[u];
+            if (B.u_sel[u] != sel) lo = hi = 0;
+            W.rng[lane] = make_uint2(lo, hi);
+            W.qg[lane] = qi;
+            W.ql[lane] = qi - P.reqs[B.qreq[qi]].q_first;
+            W.ea[lane] = B.qf[4 * (uint64_t)qi + 0];
+            W.eb[lane] = B.qf[4 * (uint64_t)qi + 1];
+            W.ua[lane] = B.qf[4 * (uint64_t)qi + 2];
+            W.ub[lane] = B.qf[4 * (uint64_t)qi + 3];
+            if (PASS == PASS_COUNT) {
+                const uint32_t a = max(lo, s0), bnd = min(hi, s1);
+                acc_tests += bnd > a ? bnd - a : 0u;
+            }
         }
         __syncwarp();
 
         const uint32_t nrec = s1 - s0;
         const uint32_t nch = (nrec + PK_CH - 1) / PK_CH;
         if (lane == 0) {
-            for (uint32_t k = 0; k < 2 && k < nch; k++) {
-                uint32_t cs = s0 + k * PK_CH, cn = min((uint32_t)PK_CH, s1 - cs);
-                mbar_arrive_tx(&W.bar[k], cn * (uint32_t)sizeof(RecF));
-                bulk_g2s(&W.stage[k][0], recs + cs, cn * (uint32_t)sizeof(RecF), &W.bar[k]);
+            for (uint32_t c = 0; c < 2 && c < nch; c++) {
+                const uint32_t cs = s0 + c * PK_CH, cn = min((uint32_t)PK_CH, s1 - cs);
+                mbar_arrive_tx(&W.bar[c], cn * (uint32_t)sizeof(RecF));
+                bulk_g2s(&W.stage[c][0], recs + cs, cn * (uint32_t)sizeof(RecF), &W.bar[c]);
             }
         }
         pending[0] = nch > 0;
         pending[1] = nch > 1;
 
         uint32_t qn = 0, hits = 0;
-        const uint64_t wbase = PASS == PASS_WRITE ? P.tile_off[t] : 0;
-        const uint64_t wend = PASS == PASS_WRITE ? P.tile_off[t + 1] : 0;
+        const uint64_t wbase = PASS == PASS_WRITE ? B.tile_off[t] : 0;
+        const uint64_t wend = PASS == PASS_WRITE ? B.tile_off[t + 1] : 0;
 
-        auto flush = [&](uint32_t k) {
-            uint32_t item = (uint32_t)lane < k ? W.queue[lane] : 0u;
+        auto flush = [&](uint32_t nflush) {
+            const uint32_t item = (uint32_t)lane < nflush ? W.queue[lane] : 0u;
             __syncwarp();
-            if (qn > k && (uint32_t)lane < qn - k) W.queue[lane] = W.queue[k + lane];
+            if (qn > nflush && (uint32_t)lane < qn - nflush) W.queue[lane] = W.queue[nflush + lane];
             __syncwarp();
             bool h = false;
             double tin = 0.0, tout = 0.0;
-            uint32_t qlane = item >> 27, eid = 0;
-            if ((uint32_t)lane < k) {
-                uint32_t pos = s0 + (item & 0x07ffffffu);
+            const uint32_t m = item >> 27;
+            uint32_t eid = 0;
+            if ((uint32_t)lane < nflush) {
+                const uint32_t pos = s0 + (item & 0x07ffffffu);
                 eid = ids ? ids[pos] : pos;
                 const SegD e = P.seg[eid];
-                const QueryD q = W.qd[qlane];
+                const QueryD q = B.qd[W.qg[m]];
                 Quad qd;
-                if (pair_quad(q, e, P.dd, qd) && quad_hit(qd)) {
+                if (pair_quad(q, e, q.pad, qd) && quad_hit(qd)) {
                     h = true;
                     if (PASS == PASS_WRITE) quad_interval(qd, &tin, &tout);
                 }
             }
-            unsigned hm = __ballot_sync(FULL, h);
+            const unsigned hm = __ballot_sync(FULL, h);
             if (PASS == PASS_WRITE && h) {
-                uint64_t o = wbase + hits + __popc(hm & lt_mask);
+                const uint64_t o = wbase + hits + __popc(hm & lt_mask);
                 if (o < wend) {
-                    P.out_q[o] = W.qorig[qlane];
-                    P.out_e[o] = P.orig[eid];
-                    P.out_tin[o] = tin;
-                    P.out_tout[o] = tout;
+                    B.out_q[o] = W.ql[m];
+                    B.out_e[o] = P.orig[eid];
+                    B.out_tin[o] = tin;
+                    B.out_tout[o] = tout;
                 }
             }
             hits += __popc(hm);
-            acc_exact += k;
-            qn -= k;
+            acc_exact += nflush;
+            qn -= nflush;
         };
 
-        for (uint32_t k = 0; k < nch && !abort; k++) {
-            const int st = k & 1;
+        for (uint32_t c = 0; c < nch && !abort; c++) {
+            const int st = c & 1;
             if (!mbar_wait_bounded(&W.bar[st], parity[st])) {
                 abort = true;
                 break;
             }
             parity[st] ^= 1u;
             pending[st] = false;
-            const uint32_t cs = s0 + k * PK_CH;
+            const uint32_t cs = s0 + c * PK_CH;
             const uint32_t cn = min((uint32_t)PK_CH, s1 - cs);
-            const RecF *buf = &W.stage[st][0];
-            for (uint32_t j = 0; j < cn; j++) {
-                const RecF r = buf[j];
+            for (uint32_t bb = 0; bb < cn; bb += 32) {
+                const uint32_t j = bb + lane;
+                const bool inb = j < cn;
+                const RecF r = W.stage[st][inb ? j : 0];
                 const uint32_t pos = cs + j;
-                const bool pass = act && pos >= qlo && pos < qhi && prefilter(r, qa, qb, P.d2u);
-                const unsigned m = __ballot_sync(FULL, pass);
-                if (m) {
-                    if (pass) W.queue[qn + __popc(m & lt_mask)] = ((uint32_t)lane << 27) | (pos - s0);
-                    qn += __popc(m);
-                    if (qn >= 32) {
-                        __syncwarp();
-                        flush(32);
+                const uint32_t bstart = cs + bb, bend = cs + min(cn, bb + 32);
+                for (uint32_t mm = 0; mm < count; mm++) {
+                    const uint2 rg = W.rng[mm];
+                    if (rg.y <= bstart || rg.x >= bend) continue;  // warp-uniform
+                    bool p = inb && pos >= rg.x && pos < rg.y && filter_box(r, W.ea[mm], W.eb[mm]);
+                    if (!__any_sync(FULL, p)) continue;
+                    p = p && filter_gap(r, W.ua[mm], W.ub[mm]);
+                    const unsigned bm = __ballot_sync(FULL, p);
+                    if (bm) {
+                        if (p) W.queue[qn + __popc(bm & lt_mask)] = (mm << 27) | (pos - s0);
+                        qn += __popc(bm);
+                        if (qn >= 32) {
+                            __syncwarp();
+                            flush(32);
+                        }
                     }
                 }
             }
             __syncwarp();
-            if (k + 2 < nch) {
+            if (c + 2 < nch) {
                 if (lane == 0) {
-                    uint32_t ns = s0 + (k + 2) * PK_CH, nn = min((uint32_t)PK_CH, s1 - ns);
+                    const uint32_t ns = s0 + (c + 2) * PK_CH, nn = min((uint32_t)PK_CH, s1 - ns);
                     mbar_arrive_tx(&W.bar[st], nn * (uint32_t)sizeof(RecF));
                     bulk_g2s(&W.stage[st][0], recs + ns, nn * (uint32_t)sizeof(RecF), &W.bar[st]);
                 }
@@ -575,15 +553,15 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pair(PairParams P)
             flush(qn);
         }
         if (PASS == PASS_COUNT) {
-            if (lane == 0) P.tile_hits[t] = hits;
+            if (lane == 0) B.tile_hits[t] = hits;
             acc_hits += hits;
         } else {
-            if (lane == 0 && wbase + hits != wend) atomicOr(P.status, DEV_ERR_INTERNAL);
+            if (lane == 0 && wbase + hits != wend) atomicOr(B.status, DEV_ERR_INTERNAL);
         }
         __syncwarp();
     }
     if (abort) {
-        if (lane == 0) atomicOr(P.status, DEV_ERR_TIMEOUT);
+        if (lane == 0) atomicOr(B.status, DEV_ERR_TIMEOUT);
         // let copies still in flight land before the shared memory is released
         for (int st = 0; st < 2; st++)
             if (pending[st]) mbar_wait_bounded(&W.bar[st], parity[st]);
@@ -591,9 +569,9 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pair(PairParams P)
     if (PASS == PASS_COUNT) {
         for (int o = 16; o; o >>= 1) acc_tests += __shfl_xor_sync(FULL, acc_tests, o);
         if (lane == 0) {
-            atomicAdd(&P.stats[ST_TESTS], acc_tests);
-            atomicAdd(&P.stats[ST_EXACT], acc_exact);
-            atomicAdd(&P.stats[ST_HITS], acc_hits);
+            atomicAdd(&B.stats[ST_TESTS], acc_tests);
+            atomicAdd(&B.stats[ST_EXACT], acc_exact);
+            atomicAdd(&B.stats[ST_HITS], acc_hits);
         }
     }
 }
@@ -619,11 +597,23 @@ ts_status pair_grid(int *blocks)
     return TS_OK;
 }
 
-}  // namespace
-
-// ---------------------------------------------------------------------------------------------
-// host orchestration of one plain search
-// ---------------------------------------------------------------------------------------------
+void fill_pair_params(PairParams &P, const Index *ix, const ReqDesc *reqs, const PipeBufs &b,
+                      const PipeCaps &c)
+{
+    P.b = b;
+    P.reqs = reqs;
+    for (int k = 0; k < 3; k++) {
+        P.rec[k] = ix->st_rec[k];
+        P.ids[k] = ix->st_ids[k];
+    }
+    P.rec[SEL_T] = ix->rec;
+    P.ids[SEL_T] = nullptr;
+    P.rec[SEL_GRID] = ix->ga_rec;
+    P.ids[SEL_GRID] = ix->ga;
+    P.seg = ix->seg;
+    P.orig = ix->orig;
+    P.tcap = c.tiles;
+}
 
 // Two CUDA events bracketing one kernel launch on its stream.
 struct EventPair {
@@ -648,22 +638,162 @@ struct EventPair {
 };
 
 // Smallest float >= x (host).
-static float float_up(double x)
+float float_up(double x)
 {
     float f = (float)x;
     if ((double)f < x) f = nextafterf(f, INFINITY);
     return f;
 }
 
-static ts_status read_dev_status(uint32_t st)
+int bits_for(uint64_t v)
+{
+    int b = 0;
+    while (b < 64 && (v >> b) != 0) b++;
+    return b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// pipeline stages
+// ---------------------------------------------------------------------------------------------
+int key_bits(const Index *ix, uint32_t nreq)
+{
+    (void)nreq;
+    uint64_t maxlen = ix->n;
+    for (int d = 0; d < 3; d++) maxlen = std::max<uint64_t>(maxlen, ix->st_len[d]);
+    maxlen = std::max<uint64_t>(maxlen, ix->g_len);
+    return bits_for(maxlen);  // bits of a range start
+}
+
+void fill_req(ReqDesc &r, const ts_query_params *qp, uint32_t q_first, uint32_t q_count)
+{
+    r.d = qp->d;
+    r.dd = qp->d * qp->d;
+    r.t_start = qp->t_start;
+    r.t_end = qp->t_end;
+    r.q_first = q_first;
+    r.q_count = q_count;
+    r.d_up = float_up(qp->d);
+    r.d2u = float_up(r.dd * (1.0 + 1e-6));
+}
+
+ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq,
+                       const ReqDesc *reqs, uint32_t nreq, const PipeBufs &b, const PipeCaps &c,
+                       cudaStream_t s)
+{
+    TS_CUDA(cudaMemsetAsync(b.stats, 0, sizeof(unsigned long long) * ST_NSLOTS, s));
+    TS_CUDA(cudaMemsetAsync(b.status, 0, sizeof(uint32_t), s));
+    TS_CUDA(cudaMemsetAsync(b.counters, 0, sizeof(uint32_t) * 2, s));
+    TS_CUDA(cudaMemsetAsync(b.req_units, 0, sizeof(uint32_t) * nreq, s));
+    PrepParams P;
+    for (int k = 0; k < 8; k++) P.f[k] = cols[k];
+    P.nq = nq;
+    P.kind = ix->kind;
+    P.reqs = reqs;
+    P.nreq = nreq;
+    P.lo_bits = key_bits(ix, nreq);
+    P.n = ix->n;
+    P.m = ix->m;
+    P.tmin = ix->tmin;
+    P.tmax = ix->tmax;
+    P.bin_start = ix->bin_start;
+    P.bin_pmax = ix->bin_pmax;
+    P.bin_off = ix->bin_off;
+    for (int d = 0; d < 3; d++) {
+        P.v[d] = ix->v[d];
+        P.sub_lo[d] = ix->sub_lo[d];
+        P.sub_w[d] = ix->sub_w[d];
+        P.st_off[d] = ix->st_off[d];
+        P.g_lo[d] = ix->g_lo[d];
+        P.g_w[d] = ix->g_w[d];
+        P.longest[d] = ix->longest[d];
+    }
+    P.g = ix->g;
+    P.b = b;
+    if (nq) {
+        k_qprep<<<nblk(nq), TPB, 0, s>>>(P);
+        TS_LAUNCHED();
+    }
+    (void)c;
+    return TS_OK;
+}
+
+ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const PipeCaps &c,
+                          cudaStream_t s)
+{
+    (void)c;
+    if (!nq) return TS_OK;
+    k_grid_units<<<nblk(nq), TPB, 0, s>>>(nq, key_bits(ix, 1), ix->g, ix->g_off, b);
+    TS_LAUNCHED();
+    return TS_OK;
+}
+
+ts_status pipe_group(const Index *ix, uint32_t nreq, const PipeBufs &b, const PipeCaps &c,
+                     cudaStream_t s)
+{
+    const int bits = key_bits(ix, nreq) + 3 + bits_for(nreq > 1 ? nreq - 1 : 0);
+    TS_CHECK(radix_sort_u64(b.keys, b.vals, c.units, bits, s));
+    k_req_scan<<<1, 32, 0, s>>>(nreq, b);
+    TS_LAUNCHED();
+    k_groups<<<nblk(c.groups), TPB, 0, s>>>(nreq, c.groups, b);
+    TS_LAUNCHED();
+    TS_CHECK(scan_u32_to_u64(b.ntiles, b.tile_base, c.groups, s));
+    k_hdr<<<1, 1, 0, s>>>(c.groups, c.tiles, b);
+    TS_LAUNCHED();
+    return TS_OK;
+}
+
+ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,
+                     cudaStream_t s)
+{
+    int blocks = 0;
+    TS_CHECK(pair_grid(&blocks));
+    PairParams P;
+    fill_pair_params(P, ix, reqs, b, c);
+    if (c.tiles) {
+        TS_CUDA(cudaMemsetAsync(b.tile_hits, 0, sizeof(uint32_t) * c.tiles, s));
+        k_pair<PASS_COUNT><<<blocks, PK_THREADS, sizeof(WarpSmem) * PK_WARPS, s>>>(P);
+        TS_LAUNCHED();
+    }
+    return TS_OK;
+}
+
+ts_status pipe_scan_rows(const PipeBufs &b, const PipeCaps &c, cudaStream_t s)
+{
+    return scan_u32_to_u64(b.tile_hits, b.tile_off, c.tiles, s);
+}
+
+ts_status pipe_write(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,
+                     cudaStream_t s)
+{
+    int blocks = 0;
+    TS_CHECK(pair_grid(&blocks));
+    PairParams P;
+    fill_pair_params(P, ix, reqs, b, c);
+    if (c.tiles) {
+        k_pair<PASS_WRITE><<<blocks, PK_THREADS, sizeof(WarpSmem) * PK_WARPS, s>>>(P);
+        TS_LAUNCHED();
+    }
+    return TS_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// host orchestration of one plain search
+// ---------------------------------------------------------------------------------------------
+ts_status read_dev_status(uint32_t st)
 {
     if (st & DEV_ERR_INVALID) {
         set_error("invalid query segment (NaN/Inf or t_end <= t_start)");
         return TS_ERR_INVALID_ARG;
     }
     if (st & DEV_ERR_TIMEOUT) {
-        set_error("a bounded device wait ran out (TMA copy did not complete)");
+        set_error("a bounded device wait ran out (bulk copy did not complete)");
         return TS_ERR_TIMEOUT;
+    }
+    if (st & DEV_ERR_OVERFLOW) {
+        set_error("a work buffer capacity was exceeded");
+        return TS_ERR_CAPACITY;
     }
     if (st) {
         set_error("search: device status 0x%x", st);
@@ -672,112 +802,11 @@ static ts_status read_dev_status(uint32_t st)
     return TS_OK;
 }
 
-// Runs query preparation and grouping; fills the work buffers. Returns the device pointers the
-// pair kernel needs through P (outputs left unset).
-static ts_status prepare(const Index *ix, const double *const cols[8], uint64_t nq,
-                         const ts_query_params *qp, cudaStream_t s, SearchWork &w, PairParams &P)
-{
-    TS_CHECK(w.qd.alloc(sizeof(QueryD) * nq, s));
-    TS_CHECK(w.qf.alloc(sizeof(float4) * 2 * nq, s));
-    TS_CHECK(w.qlo.alloc(sizeof(uint32_t) * nq, s));
-    TS_CHECK(w.qhi.alloc(sizeof(uint32_t) * nq, s));
-    TS_CHECK(w.qsel.alloc(sizeof(uint32_t) * nq, s));
-    TS_CHECK(w.keys.alloc(sizeof(uint64_t) * nq, s));
-    TS_CHECK(w.vals.alloc(sizeof(uint32_t) * nq, s));
-    TS_CHECK(w.flags.alloc(sizeof(uint32_t) * nq, s));
-    TS_CHECK(w.gid.alloc(sizeof(uint32_t) * (nq + 1), s));
-    TS_CHECK(w.groups.alloc(sizeof(Group) * nq, s));
-    TS_CHECK(w.ntiles.alloc(sizeof(uint32_t) * nq, s));
-    TS_CHECK(w.tile_base.alloc(sizeof(uint64_t) * (nq + 1), s));
-    TS_CHECK(w.hdr.alloc(sizeof(uint32_t) * HDR_N, s));
-    TS_CHECK(w.stats.alloc(sizeof(unsigned long long) * ST_NSLOTS, s));
-    TS_CHECK(w.status.alloc(sizeof(uint32_t), s));
-    TS_CHECK(w.counters.alloc(sizeof(uint32_t) * 2, s));
-    TS_CUDA(cudaMemsetAsync(w.stats.p, 0, sizeof(unsigned long long) * ST_NSLOTS, s));
-    TS_CUDA(cudaMemsetAsync(w.status.p, 0, sizeof(uint32_t), s));
-    TS_CUDA(cudaMemsetAsync(w.counters.p, 0, sizeof(uint32_t) * 2, s));
-    TS_CUDA(cudaMemsetAsync(w.ntiles.p, 0, sizeof(uint32_t) * nq, s));
-
-    PrepParams pp;
-    for (int k = 0; k < 8; k++) pp.f[k] = cols[k];
-    pp.nq = nq;
-    pp.kind = ix->kind;
-    pp.d = qp->d;
-    pp.Ts = qp->t_start;
-    pp.Te = qp->t_end;
-    pp.n = ix->n;
-    pp.m = ix->m;
-    pp.tmin = ix->tmin;
-    pp.tmax = ix->tmax;
-    pp.bin_start = ix->bin_start;
-    pp.bin_pmax = ix->bin_pmax;
-    pp.bin_off = ix->bin_off;
-    for (int d = 0; d < 3; d++) {
-        pp.v[d] = ix->v[d];
-        pp.sub_lo[d] = ix->sub_lo[d];
-        pp.sub_w[d] = ix->sub_w[d];
-        pp.st_off[d] = ix->st_off[d];
-    }
-    pp.qd = w.qd.as<QueryD>();
-    pp.qf = w.qf.as<float4>();
-    pp.qlo = w.qlo.as<uint32_t>();
-    pp.qhi = w.qhi.as<uint32_t>();
-    pp.qsel = w.qsel.as<uint32_t>();
-    pp.keys = w.keys.as<uint64_t>();
-    pp.vals = w.vals.as<uint32_t>();
-    pp.stats = w.stats.as<unsigned long long>();
-    pp.status = w.status.as<uint32_t>();
-    k_qprep<<<nblk(nq), TPB, 0, s>>>(pp);
-    TS_LAUNCHED();
-
-    TS_CHECK(radix_sort_u64(w.keys.as<uint64_t>(), w.vals.as<uint32_t>(), nq, 64, s));
-    k_group_mark<<<nblk(nq), TPB, 0, s>>>(w.keys.as<uint64_t>(), nq,
-                                          w.stats.as<unsigned long long>(), w.flags.as<uint32_t>());
-    TS_LAUNCHED();
-    TS_CHECK(scan_u32(w.flags.as<uint32_t>(), w.gid.as<uint32_t>(), nq, w.status.as<uint32_t>(), s));
-    k_group_fill<<<nblk(nq), TPB, 0, s>>>(w.keys.as<uint64_t>(), w.vals.as<uint32_t>(), nq,
-                                          w.stats.as<unsigned long long>(), w.flags.as<uint32_t>(),
-                                          w.gid.as<uint32_t>(), w.qlo.as<uint32_t>(),
-                                          w.qhi.as<uint32_t>(), w.groups.as<Group>(),
-                                          w.ntiles.as<uint32_t>());
-    TS_LAUNCHED();
-    TS_CHECK(scan_u32_to_u64(w.ntiles.as<uint32_t>(), w.tile_base.as<uint64_t>(), nq, s));
-    k_hdr<<<1, 1, 0, s>>>(w.stats.as<unsigned long long>(), w.gid.as<uint32_t>(),
-                          w.tile_base.as<uint64_t>(), nq, w.hdr.as<uint32_t>(),
-                          w.stats.as<unsigned long long>());
-    TS_LAUNCHED();
-
-    P = PairParams{};
-    P.groups = w.groups.as<Group>();
-    P.tile_base = w.tile_base.as<uint64_t>();
-    P.hdr = w.hdr.as<uint32_t>();
-    P.qval = w.vals.as<uint32_t>();
-    P.qd = w.qd.as<QueryD>();
-    P.qf = w.qf.as<float4>();
-    P.qlo = w.qlo.as<uint32_t>();
-    P.qhi = w.qhi.as<uint32_t>();
-    for (int k = 0; k < 3; k++) {
-        P.rec[k] = ix->st_rec[k];
-        P.ids[k] = ix->st_ids[k];
-    }
-    P.rec[SEL_T] = ix->rec;
-    P.ids[SEL_T] = nullptr;
-    P.rec[SEL_GRID] = ix->ga_rec;
-    P.ids[SEL_GRID] = ix->ga;
-    P.seg = ix->seg;
-    P.orig = ix->orig;
-    P.dd = qp->d * qp->d;
-    P.d2u = float_up(P.dd * (1.0 + 1e-6));
-    P.stats = w.stats.as<unsigned long long>();
-    P.status = w.status.as<uint32_t>();
-    return TS_OK;
-}
-
-static ts_status device_cols(const ts_segments *q, cudaStream_t s, DevBuf &copy, const double *cols[8])
+ts_status device_cols(const ts_segments *q, cudaStream_t s, DevBuf &copy, const double *cols[8])
 {
     const double *src[8] = {q->x0, q->y0, q->z0, q->t0, q->x1, q->y1, q->z1, q->t1};
     for (int k = 0; k < 8; k++)
-        if (!src[k]) {
+        if (!src[k] && q->n) {
             set_error("NULL query column %d", k);
             return TS_ERR_INVALID_ARG;
         }
@@ -794,7 +823,7 @@ static ts_status device_cols(const ts_segments *q, cudaStream_t s, DevBuf &copy,
     return TS_OK;
 }
 
-static ts_status check_query_params(const ts_query_params *qp)
+ts_status check_query_params(const ts_query_params *qp)
 {
     if (!qp) {
         set_error("NULL query parameters");
@@ -811,6 +840,120 @@ static ts_status check_query_params(const ts_query_params *qp)
     return TS_OK;
 }
 
+namespace {
+
+// Work buffers of a plain search, allocated stage by stage at their exact sizes.
+struct PlainWork {
+    DevBuf qd, qf, qreq, qcell, qnu, quoff, u_q, u_lo, u_hi, u_sel, keys, vals, req, groups, segs,
+        ntiles, tile_base, tiles, tile_off, ctl, reqdesc;
+};
+
+ts_status alloc_units(PlainWork &w, PipeBufs &b, uint64_t units, cudaStream_t s)
+{
+    TS_CHECK(w.u_q.alloc(sizeof(uint32_t) * units, s));
+    TS_CHECK(w.u_lo.alloc(sizeof(uint32_t) * units, s));
+    TS_CHECK(w.u_hi.alloc(sizeof(uint32_t) * units, s));
+    TS_CHECK(w.u_sel.alloc(sizeof(uint32_t) * units, s));
+    TS_CHECK(w.keys.alloc(sizeof(uint64_t) * units, s));
+    TS_CHECK(w.vals.alloc(sizeof(uint32_t) * units, s));
+    b.u_q = w.u_q.as<uint32_t>();
+    b.u_lo = w.u_lo.as<uint32_t>();
+    b.u_hi = w.u_hi.as<uint32_t>();
+    b.u_sel = w.u_sel.as<uint32_t>();
+    b.keys = w.keys.as<uint64_t>();
+    b.vals = w.vals.as<uint32_t>();
+    return TS_OK;
+}
+
+ts_status plain_prepare(const Index *ix, const double *const cols[8], uint64_t nq,
+                        const ts_query_params *qp, cudaStream_t s, PlainWork &w, PipeBufs &b,
+                        PipeCaps &c, bool group)
+{
+    b = PipeBufs{};
+    c = PipeCaps{};
+    c.nq = nq;
+    c.nreq = 1;
+    ReqDesc rd;
+    fill_req(rd, qp, 0, (uint32_t)nq);
+    TS_CHECK(w.reqdesc.alloc(sizeof(ReqDesc), s));
+    TS_CUDA(cudaMemcpyAsync(w.reqdesc.p, &rd, sizeof(ReqDesc), cudaMemcpyHostToDevice, s));
+    TS_CHECK(w.qd.alloc(sizeof(QueryD) * nq, s));
+    TS_CHECK(w.qf.alloc(sizeof(float4) * 4 * nq, s));
+    TS_CHECK(w.qreq.alloc(sizeof(uint32_t) * nq, s));
+    // control block: hdr (8 u32), stats (ST_NSLOTS u64), status, 2 counters
+    TS_CHECK(w.ctl.alloc(256, s));
+    TS_CHECK(w.req.alloc(sizeof(uint32_t) * 8, s));
+    b.qd = w.qd.as<QueryD>();
+    b.qf = w.qf.as<float4>();
+    b.qreq = w.qreq.as<uint32_t>();
+    b.hdr = w.ctl.as<uint32_t>();
+    b.stats = reinterpret_cast<unsigned long long *>(w.ctl.as<uint32_t>() + 8);
+    b.status = w.ctl.as<uint32_t>() + 8 + 2 * ST_NSLOTS;
+    b.counters = b.status + 1;
+    b.req_units = w.req.as<uint32_t>();
+    b.ustart = b.req_units + 1;
+    b.req_groups = b.req_units + 3;
+    b.gstart = b.req_units + 4;
+    uint64_t units = nq;
+    if (ix->kind == TS_INDEX_SPATIAL) {
+        TS_CHECK(w.qcell.alloc(sizeof(uint32_t) * 2 * nq, s));
+        TS_CHECK(w.qnu.alloc(sizeof(uint32_t) * nq, s));
+        TS_CHECK(w.quoff.alloc(sizeof(uint32_t) * (nq + 1), s));
+        b.qcell = w.qcell.as<uint32_t>();
+        b.qnu = w.qnu.as<uint32_t>();
+        b.quoff = w.quoff.as<uint32_t>();
+    } else {
+        TS_CHECK(alloc_units(w, b, nq, s));
+    }
+    TS_CHECK(pipe_prepare(ix, cols, nq, w.reqdesc.as<ReqDesc>(), 1, b, c, s));
+    if (ix->kind == TS_INDEX_SPATIAL) {
+        TS_CHECK(scan_u32(b.qnu, b.quoff, nq, b.status, s));
+        uint32_t total = 0;
+        TS_CUDA(cudaMemcpyAsync(&total, b.quoff + nq, 4, cudaMemcpyDeviceToHost, s));
+        TS_CUDA(cudaStreamSynchronize(s));
+        units = total;
+        TS_CHECK(alloc_units(w, b, units, s));
+        TS_CHECK(pipe_grid_units(ix, nq, b, c, s));
+    }
+    c.units = units;
+    if (!group) return TS_OK;
+    c.groups = (units + GROUP - 1) / GROUP + 1;
+    TS_CHECK(w.groups.alloc(sizeof(uint32_t) * 3 * c.groups, s));
+    TS_CHECK(w.segs.alloc(sizeof(uint32_t) * 4 * GROUP * c.groups, s));
+    TS_CHECK(w.ntiles.alloc(sizeof(uint32_t) * c.groups, s));
+    TS_CHECK(w.tile_base.alloc(sizeof(uint64_t) * (c.groups + 1), s));
+    b.g_first = w.groups.as<uint32_t>();
+    b.g_count = b.g_first + c.groups;
+    b.g_nseg = b.g_count + c.groups;
+    b.seg_lo = w.segs.as<uint32_t>();
+    b.seg_hi = b.seg_lo + GROUP * c.groups;
+    b.seg_sel = b.seg_hi + GROUP * c.groups;
+    b.seg_t0 = b.seg_sel + GROUP * c.groups;
+    b.ntiles = w.ntiles.as<uint32_t>();
+    b.tile_base = w.tile_base.as<uint64_t>();
+    c.tiles = ~0ull;  // sized after the grouping; no overflow check in the header kernel
+    TS_CHECK(pipe_group(ix, 1, b, c, s));
+    return TS_OK;
+}
+
+ts_status copy_stats(const PipeBufs &b, cudaStream_t s, ts_search_stats *st, uint32_t *status)
+{
+    unsigned long long h[ST_NSLOTS];
+    TS_CUDA(cudaMemcpyAsync(h, b.stats, sizeof(h), cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaMemcpyAsync(status, b.status, 4, cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaStreamSynchronize(s));
+    st->n_qsegs = h[ST_QSEGS];
+    st->n_tests = h[ST_TESTS];
+    st->n_exact = h[ST_EXACT];
+    st->n_hits = h[ST_HITS];
+    st->n_tiles = h[ST_TILES];
+    st->n_groups = h[ST_GROUPS];
+    st->n_subbin = h[ST_SUBBIN];
+    return TS_OK;
+}
+
+}  // namespace
+
 ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_params *qp,
                        cudaStream_t s, SearchOut *out)
 {
@@ -823,10 +966,6 @@ ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_par
         set_error("query set larger than 2^31 - 1 segments");
         return TS_ERR_INVALID_ARG;
     }
-    if (ix->kind == TS_INDEX_SPATIAL) {
-        set_error("the spatial grid search runs through ts_search_spatial");
-        return TS_ERR_INVALID_ARG;
-    }
     *out = SearchOut{};
     const uint64_t nq = q->n;
     out->stats.n_queries = nq;
@@ -834,53 +973,39 @@ ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_par
     DevBuf qcopy;
     const double *cols[8];
     TS_CHECK(device_cols(q, s, qcopy, cols));
-    SearchWork w;
-    PairParams P;
-    TS_CHECK(prepare(ix, cols, nq, qp, s, w, P));
+    PlainWork w;
+    PipeBufs b;
+    PipeCaps c;
+    TS_CHECK(plain_prepare(ix, cols, nq, qp, s, w, b, c, true));
 
     uint32_t hdr[HDR_N];
     uint32_t st = 0;
-    TS_CUDA(cudaMemcpyAsync(hdr, w.hdr.p, sizeof(hdr), cudaMemcpyDeviceToHost, s));
-    TS_CUDA(cudaMemcpyAsync(&st, w.status.p, 4, cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaMemcpyAsync(hdr, b.hdr, sizeof(hdr), cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaMemcpyAsync(&st, b.status, 4, cudaMemcpyDeviceToHost, s));
     TS_CUDA(cudaStreamSynchronize(s));
     TS_CHECK(read_dev_status(st));
-    const uint64_t ntiles = (uint64_t)hdr[HDR_NTILES_LO] | ((uint64_t)hdr[HDR_NTILES_HI] << 32);
+    c.tiles = (uint64_t)hdr[HDR_T_LO] | ((uint64_t)hdr[HDR_T_HI] << 32);
+    TS_CHECK(w.tiles.alloc(sizeof(uint32_t) * (c.tiles ? c.tiles : 1), s));
+    TS_CHECK(w.tile_off.alloc(sizeof(uint64_t) * (c.tiles + 1), s));
+    b.tile_hits = w.tiles.as<uint32_t>();
+    b.tile_off = w.tile_off.as<uint64_t>();
 
-    int blocks = 0;
-    TS_CHECK(pair_grid(&blocks));
-    const size_t smem = sizeof(WarpSmem) * PK_WARPS;
-    TS_CHECK(w.tile_hits.alloc(sizeof(uint32_t) * (ntiles ? ntiles : 1), s));
-    TS_CHECK(w.tile_off.alloc(sizeof(uint64_t) * (ntiles + 1), s));
-    P.tile_hits = w.tile_hits.as<uint32_t>();
-    P.tile_counter = w.counters.as<uint32_t>();
     EventPair ev_count, ev_write;
     TS_CHECK(ev_count.create());
     TS_CHECK(ev_write.create());
     TS_CUDA(cudaEventRecord(ev_count.a, s));
-    if (ntiles) {
-        k_pair<PASS_COUNT><<<blocks, PK_THREADS, smem, s>>>(P);
-        TS_LAUNCHED();
-    }
+    TS_CHECK(pipe_count(ix, w.reqdesc.as<ReqDesc>(), b, c, s));
     TS_CUDA(cudaEventRecord(ev_count.b, s));
-    TS_CHECK(scan_u32_to_u64(w.tile_hits.as<uint32_t>(), w.tile_off.as<uint64_t>(), ntiles, s));
+    TS_CHECK(pipe_scan_rows(b, c, s));
     uint64_t total = 0;
-    unsigned long long hst[ST_NSLOTS];
-    TS_CUDA(cudaMemcpyAsync(&total, w.tile_off.as<uint64_t>() + ntiles, 8, cudaMemcpyDeviceToHost, s));
-    TS_CUDA(cudaMemcpyAsync(hst, w.stats.p, sizeof(hst), cudaMemcpyDeviceToHost, s));
-    TS_CUDA(cudaMemcpyAsync(&st, w.status.p, 4, cudaMemcpyDeviceToHost, s));
-    TS_CUDA(cudaStreamSynchronize(s));
+    TS_CUDA(cudaMemcpyAsync(&total, b.tile_off + c.tiles, 8, cudaMemcpyDeviceToHost, s));
+    TS_CHECK(copy_stats(b, s, &out->stats, &st));
     TS_CHECK(read_dev_status(st));
-    out->count = total;
-    out->stats.n_qsegs = hst[ST_QSEGS];
-    out->stats.n_tests = hst[ST_TESTS];
-    out->stats.n_exact = hst[ST_EXACT];
-    out->stats.n_hits = hst[ST_HITS];
-    out->stats.n_tiles = hst[ST_TILES];
-    out->stats.n_groups = hst[ST_GROUPS];
-    out->stats.n_subbin = hst[ST_SUBBIN];
+    out->stats.n_queries = nq;
     out->stats.ms_count_pass = ev_count.ms();
-    if (hst[ST_HITS] != total) {
-        set_error("hit count mismatch (%llu vs %llu)", (unsigned long long)hst[ST_HITS],
+    out->count = total;
+    if (out->stats.n_hits != total) {
+        set_error("hit count mismatch (%llu vs %llu)", (unsigned long long)out->stats.n_hits,
                   (unsigned long long)total);
         return TS_ERR_INTERNAL;
     }
@@ -894,17 +1019,15 @@ ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_par
     TS_CUDA(cudaMallocAsync((void **)&out->e, sizeof(uint32_t) * total, s));
     TS_CUDA(cudaMallocAsync((void **)&out->tin, sizeof(double) * total, s));
     TS_CUDA(cudaMallocAsync((void **)&out->tout, sizeof(double) * total, s));
-    P.tile_off = w.tile_off.as<uint64_t>();
-    P.out_q = out->q;
-    P.out_e = out->e;
-    P.out_tin = out->tin;
-    P.out_tout = out->tout;
-    P.tile_counter = w.counters.as<uint32_t>() + 1;
+    b.out_q = out->q;
+    b.out_e = out->e;
+    b.out_tin = out->tin;
+    b.out_tout = out->tout;
+    c.rows = total;
     TS_CUDA(cudaEventRecord(ev_write.a, s));
-    k_pair<PASS_WRITE><<<blocks, PK_THREADS, smem, s>>>(P);
-    TS_LAUNCHED();
+    TS_CHECK(pipe_write(ix, w.reqdesc.as<ReqDesc>(), b, c, s));
     TS_CUDA(cudaEventRecord(ev_write.b, s));
-    TS_CUDA(cudaMemcpyAsync(&st, w.status.p, 4, cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaMemcpyAsync(&st, b.status, 4, cudaMemcpyDeviceToHost, s));
     TS_CUDA(cudaStreamSynchronize(s));
     TS_CHECK(read_dev_status(st));
     out->stats.ms_write_pass = ev_write.ms();
@@ -921,22 +1044,39 @@ ts_status schedule_only(const Index *ix, const ts_segments *q, const ts_query_pa
     }
     const uint64_t nq = q->n;
     if (nq == 0) return TS_OK;
-    if (ix->kind == TS_INDEX_SPATIAL) {
-        set_error("ts_schedule: the spatial grid schedule runs through ts_search_spatial");
-        return TS_ERR_INVALID_ARG;
-    }
     DevBuf qcopy;
     const double *cols[8];
     TS_CHECK(device_cols(q, s, qcopy, cols));
-    SearchWork w;
-    PairParams P;
-    TS_CHECK(prepare(ix, cols, nq, qp, s, w, P));
-    std::vector<uint32_t> hs(nq), hl(nq), hh(nq);
+    PlainWork w;
+    PipeBufs b;
+    PipeCaps c;
+    TS_CHECK(plain_prepare(ix, cols, nq, qp, s, w, b, c, false));
     uint32_t st = 0;
-    TS_CUDA(cudaMemcpyAsync(hs.data(), w.qsel.p, 4 * nq, cudaMemcpyDeviceToHost, s));
-    TS_CUDA(cudaMemcpyAsync(hl.data(), w.qlo.p, 4 * nq, cudaMemcpyDeviceToHost, s));
-    TS_CUDA(cudaMemcpyAsync(hh.data(), w.qhi.p, 4 * nq, cudaMemcpyDeviceToHost, s));
-    TS_CUDA(cudaMemcpyAsync(&st, w.status.p, 4, cudaMemcpyDeviceToHost, s));
+    if (ix->kind == TS_INDEX_SPATIAL) {
+        // per query: number of z-runs and of candidates (sum of the runs' lengths)
+        std::vector<uint32_t> off(nq + 1), ul(c.units), uh(c.units);
+        TS_CUDA(cudaMemcpyAsync(off.data(), b.quoff, 4 * (nq + 1), cudaMemcpyDeviceToHost, s));
+        if (c.units) {
+            TS_CUDA(cudaMemcpyAsync(ul.data(), b.u_lo, 4 * c.units, cudaMemcpyDeviceToHost, s));
+            TS_CUDA(cudaMemcpyAsync(uh.data(), b.u_hi, 4 * c.units, cudaMemcpyDeviceToHost, s));
+        }
+        TS_CUDA(cudaMemcpyAsync(&st, b.status, 4, cudaMemcpyDeviceToHost, s));
+        TS_CUDA(cudaStreamSynchronize(s));
+        TS_CHECK(read_dev_status(st));
+        for (uint64_t i = 0; i < nq; i++) {
+            sel[i] = SEL_GRID;
+            lo[i] = off[i + 1] - off[i];
+            uint64_t cand = 0;
+            for (uint32_t u = off[i]; u < off[i + 1]; u++) cand += uh[u] - ul[u];
+            hi[i] = cand;
+        }
+        return TS_OK;
+    }
+    std::vector<uint32_t> hs(nq), hl(nq), hh(nq);
+    TS_CUDA(cudaMemcpyAsync(hs.data(), b.u_sel, 4 * nq, cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaMemcpyAsync(hl.data(), b.u_lo, 4 * nq, cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaMemcpyAsync(hh.data(), b.u_hi, 4 * nq, cudaMemcpyDeviceToHost, s));
+    TS_CUDA(cudaMemcpyAsync(&st, b.status, 4, cudaMemcpyDeviceToHost, s));
     TS_CUDA(cudaStreamSynchronize(s));
     TS_CHECK(read_dev_status(st));
     for (uint64_t i = 0; i < nq; i++) {

@@ -1,51 +1,71 @@
-// ts_search.cuh -- search plan shared by the plain, batched and served paths.
+// ts_search.cuh -- the search pipeline shared by the plain, batched and served paths.
+//
+// A batch holds R requests (query set, d, [t_start, t_end]); the plain search is R = 1.
+//   1. query preparation (one thread per query segment): validation, clipped window, FP64 query
+//      record, FP32 boxes, and the query's candidate units -- (array, range) pairs from the
+//      index's schedule (Sec. 4.2 / 4.3), or one unit per z-run of grid cells (Sec. 4.1);
+//   2. units sorted by (request, array, range start);
+//   3. groups of up to 32 consecutive units of one request; the union of their ranges is merged
+//      into disjoint segments, cut into tiles of PK_TILE records;
+//   4. pair kernel, count pass: per tile the number of hits;
+//   5. exclusive scan of the tile counts (row offsets; a request's rows are contiguous);
+//   6. pair kernel, write pass: rows at their offsets.
 #pragma once
 
 #include "ts_index.cuh"
 
 namespace ts {
 
-// Pair kernel geometry: 8 warps per block; each warp owns one work tile at a time and streams
-// its candidate records through two shared-memory stages of PK_CH records.
 constexpr int PK_WARPS = 8;
 constexpr int PK_THREADS = PK_WARPS * 32;
-constexpr int PK_CH = 64;          // records per stage (2 KB)
-constexpr int PK_TILE = 2048;      // candidate records per tile (multiple of PK_CH)
+constexpr int PK_CH = 128;     // records per bulk-copy stage (4 KB)
+constexpr int PK_TILE = 1024;  // records per tile (multiple of PK_CH)
+constexpr int GROUP = 32;      // units per group
 
-// Device-side header of one search (written by the grouping kernels, read by the pair kernel).
-enum { HDR_NVALID = 0, HDR_NGROUPS = 1, HDR_NTILES_LO = 2, HDR_NTILES_HI = 3, HDR_N = 4 };
+enum { HDR_U = 0, HDR_G = 1, HDR_T_LO = 2, HDR_T_HI = 3, HDR_N = 4 };
 
-struct PairParams {
-    // groups and tiles
-    const Group *groups;
-    const uint64_t *tile_base;  // ngroups + 1 (scan of tiles per group)
-    const uint32_t *hdr;
-    // queries (caller order) and the sorted-order map
-    const uint32_t *qval;       // sorted position -> caller index
-    const QueryD *qd;
-    const float4 *qf;           // 2 per query: (xmin, ymin, zmin, w0), (xmax, ymax, zmax, w1)
-    const uint32_t *qlo, *qhi;  // own candidate range per caller query
-    // candidate record arrays by selector
-    const RecF *rec[5];
-    const uint32_t *ids[5];     // NULL: record position == sorted entry
-    const SegD *seg;
-    const uint32_t *orig;
-    double dd;                  // d * d
-    float d2u;                  // FP32 upper bound of d^2 (with slack)
-    // outputs
-    uint32_t *tile_hits;        // count pass
-    const uint64_t *tile_off;   // write pass (ntiles + 1)
-    uint32_t *out_q, *out_e;
-    double *out_tin, *out_tout;
-    unsigned long long *stats;
-    uint32_t *status;
-    uint32_t *tile_counter;
+// One request of a batch (device memory).
+struct ReqDesc {
+    double d, dd, t_start, t_end;
+    uint32_t q_first, q_count;  // its queries in the batch's concatenated query arrays
+    float d_up, d2u;            // FP32 upper bounds of d and of d^2 (with slack)
 };
 
-// Workspace of one plain search.
-struct SearchWork {
-    DevBuf qd, qf, qlo, qhi, qsel, keys, vals, flags, gid, groups, ntiles, tile_base, hdr, stats,
-        status, counters, tile_hits, tile_off;
+// Device buffers of one pipeline run (pointers; ownership outside).
+struct PipeBufs {
+    // per query
+    QueryD *qd;
+    float4 *qf;          // 4 per query: expanded box lo/hi (+ window), box lo (+d2u), box hi
+    uint32_t *qreq;      // request of every query
+    uint32_t *qcell;     // grid only: 6 x 10-bit cell box packed into two u32 per query
+    uint32_t *qnu;       // grid only: units per query
+    uint32_t *quoff;     // grid only: exclusive scan of qnu (nq + 1)
+    // per unit (unit id order)
+    uint32_t *u_q, *u_lo, *u_hi, *u_sel;
+    uint64_t *keys;
+    uint32_t *vals;      // sorted unit ids after the sort
+    // per request
+    uint32_t *req_units, *ustart, *req_groups, *gstart;  // R, R+1, R, R+1
+    // groups
+    uint32_t *g_first, *g_count, *g_nseg;
+    uint32_t *seg_lo, *seg_hi, *seg_sel, *seg_t0;  // GROUP per group
+    uint32_t *ntiles;
+    uint64_t *tile_base;  // groups + 1
+    // tiles and rows
+    uint32_t *tile_hits;
+    uint64_t *tile_off;   // tiles + 1
+    uint32_t *out_q, *out_e;
+    double *out_tin, *out_tout;
+    // control
+    uint32_t *hdr;
+    unsigned long long *stats;
+    uint32_t *status;
+    uint32_t *counters;   // 2 tile counters (count pass, write pass)
+};
+
+struct PipeCaps {
+    uint64_t nq = 0, units = 0, groups = 0, tiles = 0, rows = 0;
+    uint32_t nreq = 1;
 };
 
 // Result of one search (device arrays owned by the ts_result handle).
@@ -58,9 +78,30 @@ struct SearchOut {
 
 const char *last_error();
 unsigned long long launch_count();
+
+// Plain search (R = 1) with exact-size allocations; synchronises the stream.
 ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_params *qp,
                        cudaStream_t s, SearchOut *out);
 ts_status schedule_only(const Index *ix, const ts_segments *q, const ts_query_params *qp,
                         cudaStream_t s, int32_t *sel, uint64_t *lo, uint64_t *hi);
+
+// Pipeline stages (enqueue only; no host synchronisation).
+ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq,
+                       const ReqDesc *reqs, uint32_t nreq, const PipeBufs &b, const PipeCaps &c,
+                       cudaStream_t s);
+ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const PipeCaps &c,
+                          cudaStream_t s);
+ts_status pipe_group(const Index *ix, uint32_t nreq, const PipeBufs &b, const PipeCaps &c,
+                     cudaStream_t s);
+ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,
+                     cudaStream_t s);
+ts_status pipe_scan_rows(const PipeBufs &b, const PipeCaps &c, cudaStream_t s);
+ts_status pipe_write(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,
+                     cudaStream_t s);
+int key_bits(const Index *ix, uint32_t nreq);
+ts_status read_dev_status(uint32_t st);
+ts_status check_query_params(const ts_query_params *qp);
+void fill_req(ReqDesc &r, const ts_query_params *qp, uint32_t q_first, uint32_t q_count);
+ts_status device_cols(const ts_segments *q, cudaStream_t s, DevBuf &copy, const double *cols[8]);
 
 }  // namespace ts

@@ -42,6 +42,10 @@ def _run(db, q, kind, d, Ts, Te, **kw):
     ("spatiotemporal", {"sub_bins": 1}),
     ("spatiotemporal", {"sub_bins": 3, "t_bins": 11}),
     ("spatiotemporal", {"sub_bins": 64}),
+    ("spatial", {}),
+    ("spatial", {"grid_cells": 1}),
+    ("spatial", {"grid_cells": 7}),
+    ("spatial", {"grid_cells": 100}),
 ])
 def test_tiny_config_matches_oracle(tiny, kind, kw):
     d = tiny.distances[0]
@@ -168,7 +172,7 @@ def test_analytic_cases_on_gpu():
         seg((-10, 5.005, 0), 0, (10, 5.005, 0), 20),
         seg((10, 0, 0), 20, (11, 0, 0), 21),
     ])
-    for kind in ("brute", "temporal", "spatiotemporal"):
+    for kind in ("brute", "temporal", "spatiotemporal", "spatial"):
         idx = api.ts_build_index(e, kind=kind)
         got = api.ts_search(idx, q, d, -1e9, 1e9).to_host(sort=True)
         assert got["e_idx"].tolist() == [0, 1, 2], kind
@@ -247,3 +251,33 @@ def test_device_tensor_inputs(tiny):
     got = api.ts_search(idx, qcols, 5.0, 0, 70).to_host(sort=True)
     ref = oracle.search(tiny.db, tiny.queries, 0, 70, 5.0)
     parity.compare(got, ref, tiny.db, tiny.queries, 0, 70, 5.0)
+
+
+@pytest.mark.parametrize("g", [1, 5, 50])
+def test_grid_index_and_schedule_match_oracle(tiny, g):
+    db, q = tiny.db, tiny.queries
+    d, Ts, Te = 5.0, 0.0, 70.0
+    idx = api.ts_build_index(db, kind="spatial", grid_cells=g)
+    info = idx.info()
+    tref = oracle.temporal_index(db.t0, db.t1, 1)
+    perm = tref["perm"]
+    emin = [np.minimum(db.x0, db.x1), np.minimum(db.y0, db.y1), np.minimum(db.z0, db.z1)]
+    emax = [np.maximum(db.x0, db.x1), np.maximum(db.y0, db.y1), np.maximum(db.z0, db.z1)]
+    lo, w = zip(*[oracle.grid_params(emin[k], emax[k], g) for k in range(3)])
+    assert tuple(info["grid_lo"]) == lo and tuple(info["grid_w"]) == w
+    A, off = oracle.grid1([e[perm] for e in emin], g, lo, w)
+    np.testing.assert_array_equal(api.ts_index_export(idx, "perm"), perm)
+    np.testing.assert_array_equal(api.ts_index_export(idx, "grid_a"), A)
+    np.testing.assert_array_equal(api.ts_index_export(idx, "grid_off"), off)
+    longest = [float((emax[k] - emin[k]).max()) for k in range(3)]
+    qmin = [np.minimum(q.x0, q.x1), np.minimum(q.y0, q.y1), np.minimum(q.z0, q.z1)]
+    qmax = [np.maximum(q.x0, q.x1), np.maximum(q.y0, q.y1), np.maximum(q.z0, q.z1)]
+    w0 = np.maximum(q.t0, Ts)
+    w1 = np.minimum(q.t1, Te)
+    runs, cand = oracle.grid1_candidates(g, lo, w, longest, off, qmin, qmax, w0, w1, d)
+    sel, glo, ghi = api.ts_schedule(idx, q, d, Ts, Te)
+    assert np.all(sel == 4)
+    np.testing.assert_array_equal(glo, runs)
+    np.testing.assert_array_equal(ghi, cand)
+    res = api.ts_search(idx, q, d, Ts, Te)
+    assert res.stats["n_tests"] == int(cand.sum())  # one cell per entry: no duplicate candidates

@@ -153,3 +153,59 @@ def test_fsg_hand_case():
                                       [np.array([1.2]), np.array([0.1]), np.array([0.1])],
                                       [np.array([1.3]), np.array([0.2]), np.array([0.2])], 0.05)
     assert (raw[0], uniq[0]) == (1, 1)
+
+
+def test_one_cell_grid_hand_case():
+    # g = 2 over [0,2]^3 (origin 0, width 1). Minimum corners: entry 0 (0.5, 0.2, 0.2) -> cell 0,
+    # entry 1 (0, 0, 0) -> cell 0, entry 2 (1.5, 1.5, 1.5) -> cell (1,1,1) = 7.
+    emin = np.array([[0.5, 0.2, 0.2], [0.0, 0.0, 0.0], [1.5, 1.5, 1.5]])
+    emax = np.array([[1.5, 0.4, 0.4], [0.2, 0.2, 0.2], [2.0, 2.0, 2.0]])
+    lo, w = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    A, off = oracle.grid1([emin[:, k] for k in range(3)], 2, lo, w)
+    np.testing.assert_array_equal(A, [0, 1, 2])
+    np.testing.assert_array_equal(off, [0, 2, 2, 2, 2, 2, 2, 2, 3])
+    longest = emax.max(axis=0) - 0  # per-axis largest extent: x 1.0 (entry 0), y and z 0.5
+    longest = (emax - emin).max(axis=0)
+    assert tuple(longest) == (1.0, 0.5, 0.5)
+    # query MBB x 1.2..1.3, y and z 0.1..0.2, d = 0.05: minimum corners of entries within d lie in
+    # x [0.15, 1.35] (cells 0..1), y and z [-0.45, 0.25] (cell 0): runs (0,0) and (1,0), the z-run
+    # cells (0,0,0) with 2 entries and (1,0,0) with none.
+    runs, cand = oracle.grid1_candidates(2, lo, w, longest, off, [np.array([1.2]),
+                                         np.array([0.1]), np.array([0.1])],
+                                         [np.array([1.3]), np.array([0.2]), np.array([0.2])],
+                                         np.array([0.0]), np.array([1.0]), 0.05)
+    assert (runs[0], cand[0]) == (2, 2)
+    # an empty window gives no candidates
+    runs, cand = oracle.grid1_candidates(2, lo, w, longest, off, [np.array([1.2])] * 3,
+                                         [np.array([1.3])] * 3, np.array([1.0]),
+                                         np.array([1.0]), 0.05)
+    assert (runs[0], cand[0]) == (0, 0)
+
+
+def test_one_cell_grid_candidates_cover_every_hit():
+    # every pair within d must be a candidate of the grid schedule (checked against the search)
+    from tests.cases import random_segments
+    rng = np.random.default_rng(21)
+    db = random_segments(rng, 400, box=20.0, max_len=2.0)
+    q = random_segments(rng, 60, box=20.0, max_len=2.0)
+    d = 1.5
+    emin = [np.minimum(db.x0, db.x1), np.minimum(db.y0, db.y1), np.minimum(db.z0, db.z1)]
+    emax = [np.maximum(db.x0, db.x1), np.maximum(db.y0, db.y1), np.maximum(db.z0, db.z1)]
+    g = 7
+    lo, w = zip(*[oracle.grid_params(emin[k], emax[k], g) for k in range(3)])
+    longest = [float((emax[k] - emin[k]).max()) for k in range(3)]
+    A, off = oracle.grid1(emin, g, lo, w)
+    res = oracle.search(db, q, -1e9, 1e9, d)
+    cell = {}
+    for pos, s in enumerate(A):
+        h = int(np.searchsorted(off, pos, side="right") - 1)
+        cell[int(s)] = h
+    qmin = [np.minimum(q.x0, q.x1), np.minimum(q.y0, q.y1), np.minimum(q.z0, q.z1)]
+    qmax = [np.maximum(q.x0, q.x1), np.maximum(q.y0, q.y1), np.maximum(q.z0, q.z1)]
+    for qi, ei in zip(res["q_idx"], res["e_idx"]):
+        h = cell[int(ei)]
+        c = (h // (g * g), (h // g) % g, h % g)
+        for k in range(3):
+            a = (qmin[k][qi] - d) - longest[k]
+            b = qmax[k][qi] + d
+            assert lo[k] + c[k] * w[k] <= b and (c[k] == g - 1 or lo[k] + (c[k] + 1) * w[k] > a)
