@@ -193,6 +193,37 @@ void ts_free(void *handle);
 /* Message of the last failed call on this host thread ("" if none). */
 const char *ts_last_error(void);
 
+/*
+ * All-pairs search that allocates nothing (the paper has no counterpart; this is a service of this
+ * library). It is meant for callers that cannot call cudaMalloc: code embedded in an application
+ * that owns all device memory through its own allocator or a fixed budget, where a library-side
+ * cudaMalloc would escape that accounting or fail, and latency-bound request paths where
+ * cudaMalloc/cudaFree, which may synchronise the device, are not acceptable.
+ *
+ * Same result set and FP64 test as ts_search on a TS_INDEX_BRUTE index (every query segment
+ * against every database segment, no index). db and q must be device arrays (on_host = 0); the
+ * caller provides the output arrays q_idx, e_idx, t_in, t_out of `capacity` rows (device memory).
+ * *count receives the number of rows; when it exceeds `capacity` the call returns
+ * TS_ERR_CAPACITY and writes no rows. Rows are in tile order (32 query segments x 1024 database
+ * segments); sort by (q_idx, e_idx) for a canonical order. The call synchronises `stream`.
+ *
+ * Working memory: a fixed TS_NOALLOC_SCRATCH_BYTES (32 MiB) device array that is part of the
+ * library image; every GPU that loads the library holds it until the process exits. Problems
+ * needing more than TS_NOALLOC_MAX_TILES tiles, i.e. ceil(q->n / 32) * ceil(db->n / 1024) >
+ * 2,500,000, are rejected with TS_ERR_CAPACITY before any device work. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current, so make
+ * that first call before any stream capture. All calls share the one array and it keeps the last
+ * call's contents: calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. The call makes no cudaMalloc, cudaFree or other allocating
+ * call.
+ */
+#define TS_NOALLOC_SCRATCH_BYTES (32ull << 20)
+#define TS_NOALLOC_MAX_TILES 2500000ull
+ts_status ts_search_brute_noalloc(const ts_segments *db, const ts_segments *q,
+                                  const ts_query_params *qp, uint32_t *q_idx, uint32_t *e_idx,
+                                  double *t_in, double *t_out, uint64_t capacity, uint64_t *count,
+                                  void *stream);
+
 /* Number of kernels this library has launched in this process so far (all streams, all
  * devices); the difference across a region counts the launches inside it. */
 uint64_t ts_kernel_launches(void);

@@ -96,6 +96,9 @@ SIGNATURES = {
     "ts_last_error": (ctypes.c_char_p, []),
     "ts_version": (ctypes.c_char_p, []),
     "ts_kernel_launches": (ctypes.c_uint64, []),
+    "ts_search_brute_noalloc": (_S, [ctypes.POINTER(ts_segments), ctypes.POINTER(ts_segments),
+                                     ctypes.POINTER(ts_query_params), _P, _P, _P, _P,
+                                     ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _P]),
 }
 
 

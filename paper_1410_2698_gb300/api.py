@@ -242,6 +242,33 @@ def ts_free(obj):
     obj.free()
 
 
+def ts_search_brute_noalloc(db, queries, d, t_start, t_end, q_idx, e_idx, t_in, t_out,
+                            stream=None):
+    """All-pairs search into caller-provided device arrays, without any allocation by the
+    library (for callers that cannot allocate device memory). db and queries: eight float64 CUDA
+    tensors each; q_idx, e_idx (int32/uint32) and t_in, t_out (float64): CUDA tensors of equal
+    length (the capacity). Returns (status, row count); status 4 (capacity) writes no rows."""
+    lib = _lib.load()
+    s_db, keep1 = make_segments(db)
+    s_q, keep2 = make_segments(queries)
+    if s_db.on_host or s_q.on_host:
+        raise ValueError("the no-allocation search takes device tensors only")
+    cap = int(q_idx.shape[0])
+    for t in (e_idx, t_in, t_out):
+        if int(t.shape[0]) != cap:
+            raise ValueError("output arrays must have equal length")
+    qp = _qparams(d, t_start, t_end, 0)
+    count = ctypes.c_uint64(0)
+    st = lib.ts_search_brute_noalloc(ctypes.byref(s_db), ctypes.byref(s_q), ctypes.byref(qp),
+                                     q_idx.data_ptr(), e_idx.data_ptr(), t_in.data_ptr(),
+                                     t_out.data_ptr(), cap, ctypes.byref(count),
+                                     _current_stream(stream))
+    del keep1, keep2
+    if st not in (_lib.TS_OK, 4):
+        check(st)
+    return st, int(count.value)
+
+
 def ts_kernel_launches() -> int:
     return int(_lib.load().ts_kernel_launches())
 

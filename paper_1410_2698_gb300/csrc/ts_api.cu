@@ -62,6 +62,16 @@ const char *ts_last_error(void) { return ts::last_error(); }
 
 uint64_t ts_kernel_launches(void) { return (uint64_t)ts::launch_count(); }
 
+ts_status ts_search_brute_noalloc(const ts_segments *db, const ts_segments *q,
+                                  const ts_query_params *qp, uint32_t *q_idx, uint32_t *e_idx,
+                                  double *t_in, double *t_out, uint64_t capacity, uint64_t *count,
+                                  void *stream)
+{
+    ts_status st = ts::search_brute_noalloc(db, q, qp, q_idx, e_idx, t_in, t_out, capacity,
+                                            count, (cudaStream_t)stream);
+    return st == TS_OK ? clear_error(st) : st;
+}
+
 ts_status ts_build_index(const ts_segments *db, const ts_index_params *params, void *stream,
                          ts_index **out)
 {

@@ -99,6 +99,10 @@ ts_status pipe_scan_rows(const PipeBufs &b, const PipeCaps &c, cudaStream_t s);
 ts_status pipe_write(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,
                      cudaStream_t s);
 int key_bits(const Index *ix, uint32_t nreq);
+ts_status search_brute_noalloc(const ts_segments *db, const ts_segments *q,
+                               const ts_query_params *qp, uint32_t *q_idx, uint32_t *e_idx,
+                               double *t_in, double *t_out, uint64_t capacity, uint64_t *count,
+                               cudaStream_t s);
 ts_status read_dev_status(uint32_t st);
 ts_status check_query_params(const ts_query_params *qp);
 void fill_req(ReqDesc &r, const ts_query_params *qp, uint32_t q_first, uint32_t q_count);
