@@ -187,7 +187,71 @@ ts_status ts_result_stats(const ts_result *r, ts_search_stats *stats);
 ts_status ts_result_copy_to_host(const ts_result *r, uint32_t *q_idx, uint32_t *e_idx,
                                  double *t_in, double *t_out, void *stream);
 
-/* Release a ts_index or ts_result (NULL is a no-op). Waits for the device work of the handle. */
+/* ---------------------------------------------------------------------------------------------
+ * Batched search. Many requests (each a query set with its own d and interval) run through one
+ * pipeline: one query preparation launch, one sort of all candidate ranges, one persistent pair
+ * kernel per pass pulling work tiles of all requests from a device queue. The paper searches one
+ * query set per kernel invocation (Sec. 4); batching is this library's extension for serving.
+ * ------------------------------------------------------------------------------------------- */
+
+/* One-shot batch: nreq requests qs[r] with parameters qps[r]; outs[r] receives request r's result
+ * (q_idx relative to qs[r]); the results share one device allocation that is released when the
+ * last of them is freed. Synchronises `stream`. On TS_ERR_CAPACITY (some request over its
+ * max_results) every outs[r] still carries its exact count and no rows. */
+ts_status ts_search_batch(const ts_index *idx, uint32_t nreq, const ts_segments *qs,
+                          const ts_query_params *qps, void *stream, ts_result **outs);
+
+/* Reusable batch plan with fixed capacities; every run is free of host synchronisation and, with
+ * use_graph, is captured once in a CUDA graph and replayed. */
+typedef struct ts_batch_params {
+    uint32_t max_requests;  /* requests per run */
+    uint32_t tile_records;  /* candidate records per work tile, multiple of 64 (0 = 1024) */
+    uint64_t max_queries;   /* query segments per run, all requests together */
+    uint64_t max_rows;      /* result rows per run, all requests together */
+    uint64_t max_units;     /* candidate ranges per run (0 = derived) */
+    uint64_t max_tiles;     /* work tiles per run (0 = derived) */
+    int32_t use_graph;      /* 1: capture the run in a CUDA graph once, then replay it */
+    int32_t pair_blocks;    /* blocks of the persistent pair kernel (0 = all resident) */
+} ts_batch_params;
+
+typedef struct ts_batch ts_batch;
+
+/* Outcome of the last run of a plan. */
+typedef struct ts_batch_status {
+    uint64_t rows;          /* result rows of the run (exact, also when over capacity) */
+    uint32_t nreq;
+    int32_t overflow;       /* 1: a capacity was exceeded; no rows were written */
+    ts_search_stats stats;  /* totals over all requests of the run */
+} ts_batch_status;
+
+/* Create a plan for `idx` (device memory for all capacities is allocated here, once). */
+ts_status ts_batch_create(const ts_index *idx, const ts_batch_params *params, void *stream,
+                          ts_batch **out);
+
+/* Enqueue one run of nreq <= max_requests requests on `stream` (the plan's stream when NULL).
+ * Query columns may be device pointers or host pointers (on_host = 1; copied into the plan's
+ * pinned staging by this call). Returns without waiting for the device. The plan's previous run
+ * must have been waited for. */
+ts_status ts_batch_run(ts_batch *b, uint32_t nreq, const ts_segments *qs,
+                       const ts_query_params *qps, void *stream);
+
+/* Wait for the last run and report its outcome. */
+ts_status ts_batch_wait(ts_batch *b, ts_batch_status *status);
+
+/* Rows of request r of the last run: [first, first + count) of the plan's row arrays, whose
+ * device pointers ts_batch_rows returns (valid until the next run). q_idx is relative to the
+ * request's query set. */
+ts_status ts_batch_request_rows(const ts_batch *b, uint32_t r, uint64_t *first, uint64_t *count);
+ts_status ts_batch_rows(const ts_batch *b, const uint32_t **q_idx, const uint32_t **e_idx,
+                        const double **t_in, const double **t_out);
+
+/* Copy rows [first, first + count) of the last run to host arrays (NULL = skip a field).
+ * Synchronises the plan's stream. */
+ts_status ts_batch_copy_rows(const ts_batch *b, uint64_t first, uint64_t count, uint32_t *q_idx,
+                             uint32_t *e_idx, double *t_in, double *t_out);
+
+/* Release a ts_index, ts_result or ts_batch (NULL is a no-op). Waits for the device work of the
+ * handle. */
 void ts_free(void *handle);
 
 /* Message of the last failed call on this host thread ("" if none). */

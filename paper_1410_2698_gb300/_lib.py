@@ -74,6 +74,18 @@ class ts_index_info(ctypes.Structure):
         return out
 
 
+class ts_batch_params(ctypes.Structure):
+    _fields_ = [("max_requests", ctypes.c_uint32), ("tile_records", ctypes.c_uint32),
+                ("max_queries", ctypes.c_uint64), ("max_rows", ctypes.c_uint64),
+                ("max_units", ctypes.c_uint64), ("max_tiles", ctypes.c_uint64),
+                ("use_graph", ctypes.c_int32), ("pair_blocks", ctypes.c_int32)]
+
+
+class ts_batch_status(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_uint64), ("nreq", ctypes.c_uint32),
+                ("overflow", ctypes.c_int32), ("stats", ts_search_stats)]
+
+
 _P = ctypes.c_void_p
 _S = ctypes.c_int
 # name -> (restype, argtypes); every symbol declared in include/ts.h
@@ -96,6 +108,17 @@ SIGNATURES = {
     "ts_last_error": (ctypes.c_char_p, []),
     "ts_version": (ctypes.c_char_p, []),
     "ts_kernel_launches": (ctypes.c_uint64, []),
+    "ts_search_batch": (_S, [_P, ctypes.c_uint32, ctypes.POINTER(ts_segments),
+                             ctypes.POINTER(ts_query_params), _P, ctypes.POINTER(_P)]),
+    "ts_batch_create": (_S, [_P, ctypes.POINTER(ts_batch_params), _P, ctypes.POINTER(_P)]),
+    "ts_batch_run": (_S, [_P, ctypes.c_uint32, ctypes.POINTER(ts_segments),
+                          ctypes.POINTER(ts_query_params), _P]),
+    "ts_batch_wait": (_S, [_P, ctypes.POINTER(ts_batch_status)]),
+    "ts_batch_request_rows": (_S, [_P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                   ctypes.POINTER(ctypes.c_uint64)]),
+    "ts_batch_rows": (_S, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                           ctypes.POINTER(_P)]),
+    "ts_batch_copy_rows": (_S, [_P, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P, _P]),
     "ts_search_brute_noalloc": (_S, [ctypes.POINTER(ts_segments), ctypes.POINTER(ts_segments),
                                      ctypes.POINTER(ts_query_params), _P, _P, _P, _P,
                                      ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _P]),

@@ -275,3 +275,105 @@ def ts_kernel_launches() -> int:
 
 def ts_last_error() -> str:
     return _lib.load().ts_last_error().decode()
+
+
+# ---------------------------------------------------------------------------------------------
+# batched search
+# ---------------------------------------------------------------------------------------------
+def _requests(requests):
+    """requests: list of (queries, d, t_start, t_end) or (queries, d, t_start, t_end, max_results).
+    Returns ctypes arrays of ts_segments and ts_query_params and the keep-alive list."""
+    n = len(requests)
+    segs = (_lib.ts_segments * n)()
+    qps = (_lib.ts_query_params * n)()
+    keep = []
+    for r, req in enumerate(requests):
+        q, d, ts, te = req[:4]
+        mr = req[4] if len(req) > 4 else 0
+        s, k = make_segments(q)
+        segs[r] = s
+        keep.append(k)
+        qps[r] = _qparams(d, ts, te, mr)
+    return segs, qps, keep
+
+
+def ts_search_batch(index: Index, requests, stream=None):
+    """One pipeline for many requests; returns one Result per request."""
+    lib = _lib.load()
+    segs, qps, keep = _requests(requests)
+    n = len(requests)
+    outs = (ctypes.c_void_p * n)()
+    st = lib.ts_search_batch(index.handle, n, segs, qps, _current_stream(stream), outs)
+    del keep
+    if st not in (_lib.TS_OK, 4):
+        check(st)
+    return [Result(ctypes.c_void_p(outs[r]), st) for r in range(n)]
+
+
+class BatchPlan:
+    """Reusable batched pipeline with fixed capacities (ts_batch_*), optionally replayed as a
+    CUDA graph."""
+
+    def __init__(self, index: Index, max_requests, max_queries, max_rows, tile_records=0,
+                 use_graph=True, pair_blocks=0, max_units=0, max_tiles=0, stream=None):
+        lib = _lib.load()
+        p = _lib.ts_batch_params(int(max_requests), int(tile_records), int(max_queries),
+                                 int(max_rows), int(max_units), int(max_tiles), int(use_graph),
+                                 int(pair_blocks))
+        h = ctypes.c_void_p()
+        check(lib.ts_batch_create(index.handle, ctypes.byref(p), _current_stream(stream),
+                                  ctypes.byref(h)))
+        self._h = h
+        self.index = index
+        self._keep = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def run(self, requests, stream=None):
+        lib = _lib.load()
+        segs, qps, keep = _requests(requests)
+        self._keep = (segs, qps, keep)
+        check(lib.ts_batch_run(self._h, len(requests), segs, qps, _current_stream(stream)))
+
+    def wait(self) -> dict:
+        lib = _lib.load()
+        st = _lib.ts_batch_status()
+        check(lib.ts_batch_wait(self._h, ctypes.byref(st)))
+        self._keep = None
+        return {"rows": int(st.rows), "nreq": int(st.nreq), "overflow": bool(st.overflow),
+                "stats": st.stats.as_dict()}
+
+    def request_rows(self, r):
+        lib = _lib.load()
+        first, count = ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib.ts_batch_request_rows(self._h, r, ctypes.byref(first), ctypes.byref(count)))
+        return int(first.value), int(count.value)
+
+    def request_to_host(self, r, sort=False) -> dict:
+        lib = _lib.load()
+        first, n = self.request_rows(r)
+        q = np.empty(n, dtype=np.uint32)
+        e = np.empty(n, dtype=np.uint32)
+        tin = np.empty(n, dtype=np.float64)
+        tout = np.empty(n, dtype=np.float64)
+        if n:
+            check(lib.ts_batch_copy_rows(self._h, first, n, q.ctypes.data, e.ctypes.data,
+                                         tin.ctypes.data, tout.ctypes.data))
+        out = {"q_idx": q, "e_idx": e, "t_in": tin, "t_out": tout}
+        if sort and n:
+            order = np.lexsort((e, q))
+            out = {k: v[order] for k, v in out.items()}
+        return out
+
+    def free(self):
+        if self._h:
+            _lib.load().ts_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -4,7 +4,7 @@
 #include <new>
 #include <vector>
 
-#include "ts_search.cuh"
+#include "ts_batch.cuh"
 
 
 using namespace ts;
@@ -17,6 +17,11 @@ struct ts_result {
     uint32_t magic = MAGIC_RESULT;
     cudaStream_t stream = nullptr;
     SearchOut out;
+    std::shared_ptr<RowBlock> block;  // rows shared with the other results of one batch
+};
+
+struct ts_batch {
+    BatchPlan plan;
 };
 
 namespace {
@@ -43,6 +48,12 @@ ts_status guarded(F &&f)
 
 void free_result_arrays(ts_result *r)
 {
+    if (r->block) {  // rows owned by the batch's shared block
+        r->block.reset();
+        r->out.q = r->out.e = nullptr;
+        r->out.tin = r->out.tout = nullptr;
+        return;
+    }
     cudaStream_t s = r->stream;
     if (r->out.q) cudaFreeAsync(r->out.q, s);
     if (r->out.e) cudaFreeAsync(r->out.e, s);
@@ -203,6 +214,130 @@ ts_status ts_search(const ts_index *h, const ts_segments *q, const ts_query_para
     });
 }
 
+ts_status ts_search_batch(const ts_index *h, uint32_t nreq, const ts_segments *qs,
+                          const ts_query_params *qps, void *stream, ts_result **outs)
+{
+    const Index *ix = reinterpret_cast<const Index *>(h);
+    if (!ix || ix->magic != MAGIC_INDEX || !outs) {
+        set_error("ts_search_batch: invalid index handle or NULL outs");
+        return TS_ERR_INVALID_ARG;
+    }
+    for (uint32_t r = 0; r < nreq; r++) outs[r] = nullptr;
+    return guarded([&]() -> ts_status {
+        std::vector<SearchOut> res;
+        std::shared_ptr<RowBlock> block;
+        ts_status st = search_batch(ix, nreq, qs, qps, (cudaStream_t)stream, res, block);
+        if (st != TS_OK && st != TS_ERR_CAPACITY) return st;
+        if (res.size() != nreq) {
+            if (st == TS_OK) {
+                set_error("ts_search_batch: internal result count mismatch");
+                return TS_ERR_INTERNAL;
+            }
+            return st;
+        }
+        for (uint32_t r = 0; r < nreq; r++) {
+            ts_result *o = new ts_result();
+            o->stream = (cudaStream_t)stream;
+            o->out = res[r];
+            o->block = block;
+            outs[r] = o;
+        }
+        return st == TS_OK ? clear_error(st) : st;
+    });
+}
+
+ts_status ts_batch_create(const ts_index *h, const ts_batch_params *params, void *stream,
+                          ts_batch **out)
+{
+    const Index *ix = reinterpret_cast<const Index *>(h);
+    if (!ix || ix->magic != MAGIC_INDEX || !out) {
+        set_error("ts_batch_create: invalid index handle or NULL out");
+        return TS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    return guarded([&]() -> ts_status {
+        BatchPlan *p = nullptr;
+        ts_status st = create_plan(ix, params, (cudaStream_t)stream, true, &p);
+        if (st != TS_OK) return st;
+        static_assert(sizeof(ts_batch) == sizeof(BatchPlan), "handle layout");
+        *out = reinterpret_cast<ts_batch *>(p);
+        return clear_error(TS_OK);
+    });
+}
+
+ts_status ts_batch_run(ts_batch *h, uint32_t nreq, const ts_segments *qs,
+                       const ts_query_params *qps, void *stream)
+{
+    BatchPlan *p = reinterpret_cast<BatchPlan *>(h);
+    if (!p || p->magic != MAGIC_BATCH) {
+        set_error("ts_batch_run: invalid batch handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    return guarded([&]() -> ts_status {
+        ts_status st = plan_run(p, nreq, qs, qps, (cudaStream_t)stream);
+        return st == TS_OK ? clear_error(st) : st;
+    });
+}
+
+ts_status ts_batch_wait(ts_batch *h, ts_batch_status *status)
+{
+    BatchPlan *p = reinterpret_cast<BatchPlan *>(h);
+    if (!p || p->magic != MAGIC_BATCH) {
+        set_error("ts_batch_wait: invalid batch handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    ts_status st = plan_wait(p, status);
+    return st == TS_OK ? clear_error(st) : st;
+}
+
+ts_status ts_batch_request_rows(const ts_batch *h, uint32_t r, uint64_t *first, uint64_t *count)
+{
+    const BatchPlan *p = reinterpret_cast<const BatchPlan *>(h);
+    if (!p || p->magic != MAGIC_BATCH) {
+        set_error("ts_batch_request_rows: invalid batch handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    return plan_request_rows(p, r, first, count);
+}
+
+ts_status ts_batch_rows(const ts_batch *h, const uint32_t **q_idx, const uint32_t **e_idx,
+                        const double **t_in, const double **t_out)
+{
+    const BatchPlan *p = reinterpret_cast<const BatchPlan *>(h);
+    if (!p || p->magic != MAGIC_BATCH) {
+        set_error("ts_batch_rows: invalid batch handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    if (q_idx) *q_idx = p->b.out_q;
+    if (e_idx) *e_idx = p->b.out_e;
+    if (t_in) *t_in = p->b.out_tin;
+    if (t_out) *t_out = p->b.out_tout;
+    return TS_OK;
+}
+
+ts_status ts_batch_copy_rows(const ts_batch *h, uint64_t first, uint64_t count, uint32_t *q_idx,
+                             uint32_t *e_idx, double *t_in, double *t_out)
+{
+    const BatchPlan *p = reinterpret_cast<const BatchPlan *>(h);
+    if (!p || p->magic != MAGIC_BATCH) {
+        set_error("ts_batch_copy_rows: invalid batch handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    if (first + count > p->caps.rows || first + count < first) {
+        set_error("ts_batch_copy_rows: rows beyond the plan's capacity");
+        return TS_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = p->last_stream ? p->last_stream : p->stream;
+    if (count) {
+        if (q_idx) TS_CUDA(cudaMemcpyAsync(q_idx, p->b.out_q + first, 4 * count, cudaMemcpyDeviceToHost, s));
+        if (e_idx) TS_CUDA(cudaMemcpyAsync(e_idx, p->b.out_e + first, 4 * count, cudaMemcpyDeviceToHost, s));
+        if (t_in) TS_CUDA(cudaMemcpyAsync(t_in, p->b.out_tin + first, 8 * count, cudaMemcpyDeviceToHost, s));
+        if (t_out) TS_CUDA(cudaMemcpyAsync(t_out, p->b.out_tout + first, 8 * count, cudaMemcpyDeviceToHost, s));
+    }
+    TS_CUDA(cudaStreamSynchronize(s));
+    return clear_error(TS_OK);
+}
+
 uint64_t ts_result_count(const ts_result *r)
 {
     if (!r || r->magic != MAGIC_RESULT) return 0;
@@ -258,6 +393,8 @@ void ts_free(void *handle)
     uint32_t magic = *reinterpret_cast<uint32_t *>(handle);
     if (magic == MAGIC_INDEX) {
         destroy_index(reinterpret_cast<Index *>(handle));
+    } else if (magic == MAGIC_BATCH) {
+        destroy_plan(reinterpret_cast<BatchPlan *>(handle));
     } else if (magic == MAGIC_RESULT) {
         ts_result *r = reinterpret_cast<ts_result *>(handle);
         free_result_arrays(r);

@@ -1,0 +1,72 @@
+// ts_batch.cuh -- batch plans (reusable pipelines with fixed capacities) and shared row blocks.
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "ts_search.cuh"
+
+namespace ts {
+
+constexpr uint32_t MAGIC_BATCH = 0x54534254u;  // "TSBT"
+
+// Outcome of a run, written by the device into mapped pinned memory.
+struct BatchOut {
+    uint32_t hdr[8];
+    unsigned long long stats[ST_NSLOTS];
+    uint32_t status;
+    uint32_t pad[3];
+};
+
+struct BatchPlan {
+    uint32_t magic = MAGIC_BATCH;
+    const Index *ix = nullptr;
+    ts_batch_params prm{};
+    PipeCaps caps;
+    PipeBufs b{};
+    bool own_rows = true;
+    // device memory (one allocation)
+    void *dmem = nullptr;
+    size_t dbytes = 0;
+    ReqDesc *d_reqs = nullptr;
+    uint32_t *d_run = nullptr;
+    double *d_cat = nullptr;
+    unsigned long long *d_row0 = nullptr;
+    // mapped pinned host memory (one allocation)
+    void *hmem = nullptr;
+    size_t hbytes = 0;
+    ReqDesc *h_reqs = nullptr;
+    uint32_t *h_run = nullptr;
+    double *h_stage = nullptr;
+    BatchOut *h_out = nullptr;
+    unsigned long long *h_row0 = nullptr;
+    // execution
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool running = false;
+    cudaStream_t last_stream = nullptr;
+    uint32_t last_nreq = 0;
+};
+
+// Device rows shared by the results of a one-shot batch.
+struct RowBlock {
+    uint32_t *q = nullptr, *e = nullptr;
+    double *tin = nullptr, *tout = nullptr;
+    ts_status alloc(uint64_t n);
+    ~RowBlock();
+};
+
+ts_status create_plan(const Index *ix, const ts_batch_params *prm, cudaStream_t s, bool own_rows,
+                      BatchPlan **out);
+void destroy_plan(BatchPlan *p);
+ts_status plan_run(BatchPlan *p, uint32_t nreq, const ts_segments *qs, const ts_query_params *qps,
+                   cudaStream_t s);
+ts_status plan_wait(BatchPlan *p, ts_batch_status *out);
+ts_status plan_request_rows(const BatchPlan *p, uint32_t r, uint64_t *first, uint64_t *count);
+ts_status search_batch(const Index *ix, uint32_t nreq, const ts_segments *qs,
+                       const ts_query_params *qps, cudaStream_t s,
+                       std::vector<SearchOut> &outs, std::shared_ptr<RowBlock> &block);
+
+}  // namespace ts

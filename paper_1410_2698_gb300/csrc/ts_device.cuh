@@ -162,4 +162,23 @@ static __device__ __forceinline__ bool filter_gap(const RecF &r, const float4 &u
     return s2 <= ua.w;
 }
 
+// Stage 2 from the d-expanded query box: since eb >= qmax + d and ea <= qmin - d, the gap
+// r.min - qmax is at least (r.min - eb) + d, and qmin - r.max at least (ea - r.max) + d; both
+// bounds are accumulated rounding down with d_dn <= d, so the result is again a lower bound of
+// the squared separation (looser than filter_gap by a few ulps of the coordinates only).
+static __device__ __forceinline__ float gap_lo(float a, float b, float d_dn)
+{
+    return __fadd_rd(__fsub_rd(a, b), d_dn);
+}
+
+static __device__ __forceinline__ bool filter_gap_e(const RecF &r, const float4 &ea,
+                                                    const float4 &eb, float d_dn, float d2u)
+{
+    float gx = fmaxf(fmaxf(gap_lo(r.xmin, eb.x, d_dn), gap_lo(ea.x, r.xmax, d_dn)), 0.0f);
+    float gy = fmaxf(fmaxf(gap_lo(r.ymin, eb.y, d_dn), gap_lo(ea.y, r.ymax, d_dn)), 0.0f);
+    float gz = fmaxf(fmaxf(gap_lo(r.zmin, eb.z, d_dn), gap_lo(ea.z, r.zmax, d_dn)), 0.0f);
+    float s2 = __fmaf_rd(gz, gz, __fmaf_rd(gy, gy, __fmul_rd(gx, gx)));
+    return s2 <= d2u;
+}
+
 }  // namespace ts

@@ -111,9 +111,11 @@ __device__ __forceinline__ uint64_t unit_key(uint32_t r, uint32_t sel, uint32_t 
 
 __global__ void k_qprep(PrepParams P)
 {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.nq;
+    const uint64_t nq = P.b.run ? min((uint64_t)P.b.run[0], P.nq) : P.nq;
+    const uint32_t nreq = P.b.run ? P.b.run[1] : P.nreq;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = req_of(P.reqs, P.nreq, (uint32_t)i);
+        const uint32_t r = req_of(P.reqs, nreq, (uint32_t)i);
         const ReqDesc R = P.reqs[r];
         double v[8];
         bool fin = true;
@@ -144,12 +146,10 @@ __global__ void k_qprep(PrepParams P)
             fmn[d] = __double2float_rd(mn[d]);
             fmx[d] = __double2float_ru(mx[d]);
         }
-        P.b.qf[4 * i + 0] = make_float4(__fsub_rd(fmn[0], R.d_up), __fsub_rd(fmn[1], R.d_up),
+        P.b.qf[2 * i + 0] = make_float4(__fsub_rd(fmn[0], R.d_up), __fsub_rd(fmn[1], R.d_up),
                                         __fsub_rd(fmn[2], R.d_up), __double2float_rd(q.w0));
-        P.b.qf[4 * i + 1] = make_float4(__fadd_ru(fmx[0], R.d_up), __fadd_ru(fmx[1], R.d_up),
+        P.b.qf[2 * i + 1] = make_float4(__fadd_ru(fmx[0], R.d_up), __fadd_ru(fmx[1], R.d_up),
                                         __fadd_ru(fmx[2], R.d_up), __double2float_ru(q.w1));
-        P.b.qf[4 * i + 2] = make_float4(fmn[0], fmn[1], fmn[2], R.d2u);
-        P.b.qf[4 * i + 3] = make_float4(fmx[0], fmx[1], fmx[2], 0.0f);
 
         uint32_t sel = SEL_T, lo = 0, hi = 0;
         bool subbin = false;
@@ -242,13 +242,18 @@ __global__ void k_qprep(PrepParams P)
 
 // Grid index: one unit per (cx, cy) of a query's cell box, covering cells cz_a..cz_b (a z-run
 // of the row-major cell order, contiguous in the lookup array).
-__global__ void k_grid_units(uint64_t nq, int lo_bits, uint32_t g, const uint32_t *g_off,
-                             PipeBufs b)
+__global__ void k_grid_units(uint64_t nqcap, uint64_t ucap, int lo_bits, uint32_t g,
+                             const uint32_t *g_off, PipeBufs b)
 {
+    const uint64_t nq = b.run ? min((uint64_t)b.run[0], nqcap) : nqcap;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t nu = b.qnu[i];
         if (!nu) continue;
+        if ((uint64_t)b.quoff[i] + nu > ucap) {  // more runs than the unit buffers hold
+            atomicOr(b.status, DEV_ERR_OVERFLOW);
+            continue;
+        }
         const uint32_t r = b.qreq[i];
         const uint32_t w0 = b.qcell[2 * i], w1 = b.qcell[2 * i + 1];
         const uint32_t ax = w0 & 1023u, ay = (w0 >> 10) & 1023u, az = (w0 >> 20) & 1023u;
@@ -275,9 +280,10 @@ __global__ void k_grid_units(uint64_t nq, int lo_bits, uint32_t g, const uint32_
 // groups
 // ---------------------------------------------------------------------------------------------
 // Per request: unit starts (exclusive scan of its unit count) and group starts (ceil(units/32)).
-__global__ void k_req_scan(uint32_t nreq, PipeBufs b)
+__global__ void k_req_scan(uint32_t nreq_cap, PipeBufs b)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint32_t nreq = b.run ? min(b.run[1], nreq_cap) : nreq_cap;
     uint32_t us = 0, gs = 0;
     for (uint32_t r = 0; r < nreq; r++) {
         b.ustart[r] = us;
@@ -294,8 +300,9 @@ __global__ void k_req_scan(uint32_t nreq, PipeBufs b)
     b.hdr[HDR_G] = gs;
 }
 
-__global__ void k_groups(uint32_t nreq, uint64_t gcap, PipeBufs b)
+__global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, PipeBufs b)
 {
+    const uint32_t nreq = b.run ? min(b.run[1], nreq_cap) : nreq_cap;
     const uint32_t G = b.hdr[HDR_G];
     for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < gcap;
          g += (uint64_t)gridDim.x * blockDim.x) {
@@ -328,7 +335,7 @@ __global__ void k_groups(uint32_t nreq, uint64_t gcap, PipeBufs b)
             }
             if (open) {
                 slo[nseg] = clo; shi[nseg] = chi; ssel[nseg] = cs; st0[nseg] = tiles;
-                tiles += (chi - clo + PK_TILE - 1) / PK_TILE;
+                tiles += (chi - clo + tile - 1) / tile;
                 nseg++;
             }
             open = true;
@@ -336,7 +343,7 @@ __global__ void k_groups(uint32_t nreq, uint64_t gcap, PipeBufs b)
         }
         if (open) {
             slo[nseg] = clo; shi[nseg] = chi; ssel[nseg] = cs; st0[nseg] = tiles;
-            tiles += (chi - clo + PK_TILE - 1) / PK_TILE;
+            tiles += (chi - clo + tile - 1) / tile;
             nseg++;
         }
         b.g_nseg[g] = nseg;
@@ -359,7 +366,7 @@ __global__ void k_hdr(uint64_t gcap, uint64_t tcap, PipeBufs b)
 // ---------------------------------------------------------------------------------------------
 struct __align__(16) WarpSmem {
     RecF stage[2][PK_CH];
-    float4 ea[GROUP], eb[GROUP], ua[GROUP], ub[GROUP];
+    float4 ea[GROUP], eb[GROUP];
     uint2 rng[GROUP];
     uint32_t qg[GROUP];   // query index in the batch
     uint32_t ql[GROUP];   // query index within its request
@@ -377,6 +384,8 @@ struct PairParams {
     const SegD *seg;
     const uint32_t *orig;
     uint64_t tcap;
+    uint64_t rows_cap;  // write pass: rows beyond this capacity are not written (flagged)
+    uint32_t tile;      // records per tile
 };
 
 __device__ __forceinline__ uint32_t find_group(const uint64_t *base, uint32_t ng, uint64_t t)
@@ -390,7 +399,7 @@ __device__ __forceinline__ uint32_t find_group(const uint64_t *base, uint32_t ng
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(PK_THREADS, 2) k_pair(PairParams P)
+__global__ void __launch_bounds__(PK_THREADS, 3) k_pair(PairParams P)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -413,6 +422,11 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pair(PairParams P)
     const uint32_t ngroups = B.hdr[HDR_G];
     uint64_t ntiles = (uint64_t)B.hdr[HDR_T_LO] | ((uint64_t)B.hdr[HDR_T_HI] << 32);
     if (ntiles > P.tcap) ntiles = 0;  // overflow already flagged
+    if (PASS == PASS_WRITE && ntiles && B.tile_off[ntiles] > P.rows_cap) {
+        // more rows than the output holds: write none (the caller sees the exact count)
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, DEV_ERR_OVERFLOW);
+        ntiles = 0;
+    }
     unsigned long long acc_tests = 0, acc_exact = 0, acc_hits = 0;
 
     while (!abort) {
@@ -427,8 +441,8 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pair(PairParams P)
         uint32_t k = 0;
         while (k + 1 < nseg && st0[k + 1] <= lt) k++;
         const uint32_t sel = B.seg_sel[(uint64_t)g * GROUP + k];
-        const uint32_t s0 = B.seg_lo[(uint64_t)g * GROUP + k] + (lt - st0[k]) * PK_TILE;
-        const uint32_t s1 = min(B.seg_hi[(uint64_t)g * GROUP + k], s0 + PK_TILE);
+        const uint32_t s0 = B.seg_lo[(uint64_t)g * GROUP + k] + (lt - st0[k]) * P.tile;
+        const uint32_t s1 = min(B.seg_hi[(uint64_t)g * GROUP + k], s0 + P.tile);
         const uint32_t first = B.g_first[g], count = B.g_count[g];
         const RecF *recs = P.rec[sel];
         const uint32_t *ids = P.ids[sel];
@@ -442,16 +456,17 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pair(PairParams P)
             W.rng[lane] = make_uint2(lo, hi);
             W.qg[lane] = qi;
             W.ql[lane] = qi - P.reqs[B.qreq[qi]].q_first;
-            W.ea[lane] = B.qf[4 * (uint64_t)qi + 0];
-            W.eb[lane] = B.qf[4 * (uint64_t)qi + 1];
-            W.ua[lane] = B.qf[4 * (uint64_t)qi + 2];
-            W.ub[lane] = B.qf[4 * (uint64_t)qi + 3];
+            W.ea[lane] = B.qf[2 * (uint64_t)qi + 0];
+            W.eb[lane] = B.qf[2 * (uint64_t)qi + 1];
             if (PASS == PASS_COUNT) {
                 const uint32_t a = max(lo, s0), bnd = min(hi, s1);
                 acc_tests += bnd > a ? bnd - a : 0u;
             }
         }
         __syncwarp();
+        // a group's members belong to one request: its d bounds for the gap filter
+        const ReqDesc &RQ = P.reqs[B.qreq[W.qg[0]]];
+        const float d_dn = RQ.d_dn, d2u = RQ.d2u;
 
         const uint32_t nrec = s1 - s0;
         const uint32_t nch = (nrec + PK_CH - 1) / PK_CH;
@@ -514,26 +529,41 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pair(PairParams P)
             pending[st] = false;
             const uint32_t cs = s0 + c * PK_CH;
             const uint32_t cn = min((uint32_t)PK_CH, s1 - cs);
-            for (uint32_t bb = 0; bb < cn; bb += 32) {
-                const uint32_t j = bb + lane;
-                const bool inb = j < cn;
-                const RecF r = W.stage[st][inb ? j : 0];
-                const uint32_t pos = cs + j;
-                const uint32_t bstart = cs + bb, bend = cs + min(cn, bb + 32);
-                for (uint32_t mm = 0; mm < count; mm++) {
-                    const uint2 rg = W.rng[mm];
-                    if (rg.y <= bstart || rg.x >= bend) continue;  // warp-uniform
-                    bool p = inb && pos >= rg.x && pos < rg.y && filter_box(r, W.ea[mm], W.eb[mm]);
-                    if (!__any_sync(FULL, p)) continue;
-                    p = p && filter_gap(r, W.ua[mm], W.ub[mm]);
-                    const unsigned bm = __ballot_sync(FULL, p);
-                    if (bm) {
-                        if (p) W.queue[qn + __popc(bm & lt_mask)] = (mm << 27) | (pos - s0);
-                        qn += __popc(bm);
-                        if (qn >= 32) {
-                            __syncwarp();
-                            flush(32);
-                        }
+            // two records per lane: slots lane and lane + 32 of the stage
+            const bool in0 = (uint32_t)lane < cn, in1 = (uint32_t)lane + 32 < cn;
+            const RecF r0 = W.stage[st][in0 ? lane : 0];
+            const RecF r1 = W.stage[st][in1 ? lane + 32 : 0];
+            const uint32_t pos0 = cs + lane, pos1 = cs + 32 + lane;
+            const uint32_t bend = cs + cn;
+            for (uint32_t mm = 0; mm < count; mm++) {
+                const uint2 rg = W.rng[mm];
+                if (rg.y <= cs || rg.x >= bend) continue;  // warp-uniform
+                const float4 ea = W.ea[mm], eb = W.eb[mm];
+                bool p0 = in0 && filter_box(r0, ea, eb);
+                bool p1 = in1 && filter_box(r1, ea, eb);
+                if (rg.x > cs || rg.y < bend) {  // member covers part of the chunk
+                    p0 = p0 && pos0 >= rg.x && pos0 < rg.y;
+                    p1 = p1 && pos1 >= rg.x && pos1 < rg.y;
+                }
+                if (!__any_sync(FULL, p0 || p1)) continue;
+                p0 = p0 && filter_gap_e(r0, ea, eb, d_dn, d2u);
+                p1 = p1 && filter_gap_e(r1, ea, eb, d_dn, d2u);
+                const unsigned b0 = __ballot_sync(FULL, p0);
+                if (b0) {
+                    if (p0) W.queue[qn + __popc(b0 & lt_mask)] = (mm << 27) | (pos0 - s0);
+                    qn += __popc(b0);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        flush(32);
+                    }
+                }
+                const unsigned b1 = __ballot_sync(FULL, p1);
+                if (b1) {
+                    if (p1) W.queue[qn + __popc(b1 & lt_mask)] = (mm << 27) | (pos1 - s0);
+                    qn += __popc(b1);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        flush(32);
                     }
                 }
             }
@@ -613,6 +643,8 @@ void fill_pair_params(PairParams &P, const Index *ix, const ReqDesc *reqs, const
     P.seg = ix->seg;
     P.orig = ix->orig;
     P.tcap = c.tiles;
+    P.rows_cap = c.rows;
+    P.tile = c.tile;
 }
 
 // Two CUDA events bracketing one kernel launch on its stream.
@@ -642,6 +674,14 @@ float float_up(double x)
 {
     float f = (float)x;
     if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+// Largest float <= x (host).
+float float_dn(double x)
+{
+    float f = (float)x;
+    if ((double)f > x) f = nextafterf(f, -INFINITY);
     return f;
 }
 
@@ -675,6 +715,9 @@ void fill_req(ReqDesc &r, const ts_query_params *qp, uint32_t q_first, uint32_t 
     r.q_first = q_first;
     r.q_count = q_count;
     r.d_up = float_up(qp->d);
+    r.d_dn = float_dn(qp->d);
+    r.pad = 0.0f;
+    for (int k = 0; k < 8; k++) r.cols[k] = nullptr;
     r.d2u = float_up(r.dd * (1.0 + 1e-6));
 }
 
@@ -724,7 +767,7 @@ ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const
 {
     (void)c;
     if (!nq) return TS_OK;
-    k_grid_units<<<nblk(nq), TPB, 0, s>>>(nq, key_bits(ix, 1), ix->g, ix->g_off, b);
+    k_grid_units<<<nblk(nq), TPB, 0, s>>>(nq, c.units, key_bits(ix, 1), ix->g, ix->g_off, b);
     TS_LAUNCHED();
     return TS_OK;
 }
@@ -736,7 +779,7 @@ ts_status pipe_group(const Index *ix, uint32_t nreq, const PipeBufs &b, const Pi
     TS_CHECK(radix_sort_u64(b.keys, b.vals, c.units, bits, s));
     k_req_scan<<<1, 32, 0, s>>>(nreq, b);
     TS_LAUNCHED();
-    k_groups<<<nblk(c.groups), TPB, 0, s>>>(nreq, c.groups, b);
+    k_groups<<<nblk(c.groups), TPB, 0, s>>>(nreq, c.groups, c.tile, b);
     TS_LAUNCHED();
     TS_CHECK(scan_u32_to_u64(b.ntiles, b.tile_base, c.groups, s));
     k_hdr<<<1, 1, 0, s>>>(c.groups, c.tiles, b);
@@ -749,6 +792,7 @@ ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
 {
     int blocks = 0;
     TS_CHECK(pair_grid(&blocks));
+    if (c.pair_blocks > 0 && c.pair_blocks < blocks) blocks = c.pair_blocks;
     PairParams P;
     fill_pair_params(P, ix, reqs, b, c);
     if (c.tiles) {
@@ -769,6 +813,7 @@ ts_status pipe_write(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
 {
     int blocks = 0;
     TS_CHECK(pair_grid(&blocks));
+    if (c.pair_blocks > 0 && c.pair_blocks < blocks) blocks = c.pair_blocks;
     PairParams P;
     fill_pair_params(P, ix, reqs, b, c);
     if (c.tiles) {
@@ -878,7 +923,7 @@ ts_status plain_prepare(const Index *ix, const double *const cols[8], uint64_t n
     TS_CHECK(w.reqdesc.alloc(sizeof(ReqDesc), s));
     TS_CUDA(cudaMemcpyAsync(w.reqdesc.p, &rd, sizeof(ReqDesc), cudaMemcpyHostToDevice, s));
     TS_CHECK(w.qd.alloc(sizeof(QueryD) * nq, s));
-    TS_CHECK(w.qf.alloc(sizeof(float4) * 4 * nq, s));
+    TS_CHECK(w.qf.alloc(sizeof(float4) * 2 * nq, s));
     TS_CHECK(w.qreq.alloc(sizeof(uint32_t) * nq, s));
     // control block: hdr (8 u32), stats (ST_NSLOTS u64), status, 2 counters
     TS_CHECK(w.ctl.alloc(256, s));
@@ -913,6 +958,7 @@ ts_status plain_prepare(const Index *ix, const double *const cols[8], uint64_t n
         TS_CUDA(cudaStreamSynchronize(s));
         units = total;
         TS_CHECK(alloc_units(w, b, units, s));
+        c.units = units;
         TS_CHECK(pipe_grid_units(ix, nq, b, c, s));
     }
     c.units = units;

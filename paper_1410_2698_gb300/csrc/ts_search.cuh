@@ -18,7 +18,7 @@ namespace ts {
 
 constexpr int PK_WARPS = 8;
 constexpr int PK_THREADS = PK_WARPS * 32;
-constexpr int PK_CH = 128;     // records per bulk-copy stage (4 KB)
+constexpr int PK_CH = 64;      // records per bulk-copy stage (2 KB): 2 per lane
 constexpr int PK_TILE = 1024;  // records per tile (multiple of PK_CH)
 constexpr int GROUP = 32;      // units per group
 
@@ -29,13 +29,15 @@ struct ReqDesc {
     double d, dd, t_start, t_end;
     uint32_t q_first, q_count;  // its queries in the batch's concatenated query arrays
     float d_up, d2u;            // FP32 upper bounds of d and of d^2 (with slack)
+    float d_dn, pad;            // FP32 lower bound of d
+    const double *cols[8];      // batched runs: the request's query columns (device-readable)
 };
 
 // Device buffers of one pipeline run (pointers; ownership outside).
 struct PipeBufs {
     // per query
     QueryD *qd;
-    float4 *qf;          // 4 per query: expanded box lo/hi (+ window), box lo (+d2u), box hi
+    float4 *qf;          // 2 per query: d-expanded box lo (+ window start), hi (+ window end)
     uint32_t *qreq;      // request of every query
     uint32_t *qcell;     // grid only: 6 x 10-bit cell box packed into two u32 per query
     uint32_t *qnu;       // grid only: units per query
@@ -61,11 +63,14 @@ struct PipeBufs {
     unsigned long long *stats;
     uint32_t *status;
     uint32_t *counters;   // 2 tile counters (count pass, write pass)
+    const uint32_t *run;  // optional device run header {nq, nreq}: sizes read at run time (graphs)
 };
 
 struct PipeCaps {
-    uint64_t nq = 0, units = 0, groups = 0, tiles = 0, rows = 0;
+    uint64_t nq = 0, units = 0, groups = 0, tiles = 0, rows = ~0ull;
     uint32_t nreq = 1;
+    uint32_t tile = PK_TILE;  // records per tile (multiple of PK_CH)
+    int pair_blocks = 0;      // pair kernel grid (0 = all resident blocks)
 };
 
 // Result of one search (device arrays owned by the ts_result handle).

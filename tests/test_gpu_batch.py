@@ -1,0 +1,103 @@
+"""Batched search: many requests (own query sets, distances and intervals) in one pipeline, as a
+one-shot call and as a reusable plan replayed as a CUDA graph. Every request's rows must equal
+the plain single-request search, alone versus in the mix."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_2698_gb300 import api, workloads
+from paper_1410_2698_gb300.workloads import Segments
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(w, rng, n_req, max_traj=8):
+    """Requests of whole query trajectories with their own d and interval; one request is empty
+    and one has an interval before every query."""
+    seg_per = w.queries.n // len(w.query_traj_ids)
+    reqs = []
+    for r in range(n_req):
+        k = int(rng.integers(1, max_traj + 1))
+        pick = rng.choice(len(w.query_traj_ids), size=k, replace=False)
+        idx = (pick[:, None] * seg_per + np.arange(seg_per)[None, :]).ravel()
+        q = w.queries.take(idx)
+        d = float(np.exp(rng.uniform(np.log(0.5), np.log(10.0))))
+        ts = float(q.t0.min() + rng.uniform(0, 5))
+        te = float(q.t1.max() - rng.uniform(0, 5))
+        reqs.append((q, d, ts, max(ts, te)))
+    reqs.append((Segments.from_matrix(np.zeros((0, 8))), 1.0, 0.0, 10.0))
+    q0 = reqs[0][0]
+    reqs.append((q0, 2.0, -100.0, -50.0))
+    return reqs
+
+
+def _plain(idx, req):
+    q, d, ts, te = req
+    return api.ts_search(idx, q, d, ts, te).to_host(sort=True)
+
+
+def _same(a, b):
+    for k in ("q_idx", "e_idx", "t_in", "t_out"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("kind", ["temporal", "spatiotemporal", "spatial", "brute"])
+def test_one_shot_batch_equals_plain(kind):
+    w = workloads.tiny()
+    rng = np.random.default_rng(5)
+    reqs = _requests(w, rng, 9)
+    idx = api.ts_build_index(w.db, kind=kind)
+    outs = api.ts_search_batch(idx, reqs)
+    assert len(outs) == len(reqs)
+    for req, res in zip(reqs, outs):
+        _same(res.to_host(sort=True), _plain(idx, req))
+    # a request's rows against the oracle as well
+    q, d, ts, te = reqs[1]
+    parity.compare(outs[1].to_host(sort=True), oracle.search(w.db, q, ts, te, d), w.db, q, ts,
+                   te, d)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_plan_runs_equal_plain(use_graph):
+    import torch
+    w = workloads.tiny()
+    rng = np.random.default_rng(9)
+    idx = api.ts_build_index(w.db, kind="spatiotemporal")
+    plan = api.BatchPlan(idx, max_requests=16, max_queries=4000, max_rows=400000,
+                         use_graph=use_graph)
+    for trial in range(3):
+        reqs = _requests(w, rng, 6)
+        if trial == 2:  # device-resident query columns
+            reqs = [({f: torch.from_numpy(np.ascontiguousarray(getattr(q, f))).cuda()
+                      for f in Segments.FIELDS} if q.n else q, d, ts, te)
+                    for q, d, ts, te in reqs]
+        plan.run(reqs)
+        st = plan.wait()
+        assert not st["overflow"] and st["nreq"] == len(reqs)
+        total = 0
+        for r, req in enumerate(reqs):
+            got = plan.request_to_host(r, sort=True)
+            q, d, ts, te = req
+            qh = q if isinstance(q, Segments) else Segments(
+                *[q[f].cpu().numpy() for f in Segments.FIELDS], traj=np.zeros(0, np.uint32))
+            _same(got, _plain(idx, (qh, d, ts, te)))
+            total += got["q_idx"].size
+        assert total == st["rows"]
+    plan.free()
+
+
+def test_plan_reports_overflow_with_exact_count():
+    w = workloads.tiny()
+    idx = api.ts_build_index(w.db, kind="temporal")
+    plan = api.BatchPlan(idx, max_requests=2, max_queries=4000, max_rows=100, use_graph=True)
+    plan.run([(w.queries, 5.0, 0.0, 70.0)])
+    st = plan.wait()
+    ref = api.ts_search(idx, w.queries, 5.0, 0.0, 70.0).count
+    assert st["overflow"] and st["rows"] == ref
+    # the next run within capacity succeeds on the same plan and graph
+    small = w.queries.take(np.arange(3))
+    plan.run([(small, 0.5, 0.0, 70.0)])
+    st = plan.wait()
+    assert not st["overflow"]
+    _same(plan.request_to_host(0, sort=True), _plain(idx, (small, 0.5, 0.0, 70.0)))
