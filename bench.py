@@ -37,8 +37,8 @@ INTERVAL_FLOPS = 10        # FP64 flops per hit for the roots (sqrt, 2 div, clam
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="random-walk-1m")
     ap.add_argument("--indexes", default="spatiotemporal,temporal,spatial")
@@ -160,6 +160,33 @@ def roofline(tot, pair_ms):
             "peak_source": "derived: 152 SMs x lanes x 2.07 GHz (FP32), GB300 nominal (FP64)"}
 
 
+def _timed(args, stream, flush, step):
+    """Time args.steps calls of step() with CUDA events on the launching stream; the L2 is
+    flushed (a 256 MB write) before every step, outside the events."""
+    import torch
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def _max_over_ranks(x, world, dev):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -180,7 +207,8 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
     stream = torch.cuda.current_stream()
 
-    def one_step(collect=None):
+    # plain form: one ts_search per (index, d)
+    def plain_step(collect=None):
         for k in kinds:
             for d in w.distances:
                 r = api.ts_search(indexes[k], qdev, d, w.t_start, w.t_end)
@@ -188,34 +216,48 @@ def run_gpu(args):
                     collect.append((k, d, r.stats))
                 r.free()
 
+    warm = []
     for _ in range(max(args.warmup, 0)):
-        one_step()
+        plain_step(warm)
+    rows_per_batch = {k: sum(st["n_hits"] for kk, _, st in warm if kk == k) // max(args.warmup, 1)
+                      for k in kinds}
+    # batched form: one reusable plan per index, replayed as a CUDA graph; the distances are the
+    # requests of one batch
+    reqs = [(qdev, d, w.t_start, w.t_end) for d in w.distances]
+    plans = {k: api.BatchPlan(indexes[k], max_requests=len(reqs),
+                              max_queries=w.queries.n * len(reqs),
+                              max_rows=max(1 << 20, 2 * rows_per_batch[k]), use_graph=True)
+             for k in kinds}
+    batch_stats = []
+
+    def batched_step(collect=None):
+        for k in kinds:
+            plans[k].run(reqs)
+        for k in kinds:
+            st = plans[k].wait()
+            if st["overflow"]:
+                raise RuntimeError(f"batch plan overflow for {k}")
+            if collect is not None:
+                collect.append((k, st))
+
+    for _ in range(max(args.warmup, 0)):
+        batched_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    launches0 = api.ts_kernel_launches()
-    step_ms = []
+    l0 = api.ts_kernel_launches()
     per = []
+    plain_ms = _timed(args, stream, flush, lambda: plain_step(per))
+    l1 = api.ts_kernel_launches()
+    batch_ms = _timed(args, stream, flush, lambda: batched_step(batch_stats))
+    l2 = api.ts_kernel_launches()
     torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.zero_()  # L2 flush outside the timed events
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        one_step(per)
-        b.record(stream)
-        b.synchronize()
-        step_ms.append(a.elapsed_time(b))
-    torch.cuda.synchronize()
-    launches = api.ts_kernel_launches() - launches0
     clk = clocks.stop()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    plain_total = _max_over_ranks(float(sum(plain_ms)), world, dev)
+    batch_total = _max_over_ranks(float(sum(batch_ms)), world, dev)
+
     tot = {k: 0 for k in ("n_tests", "n_exact", "n_hits", "n_qsegs")}
     pair_ms = 0.0
     breakdown = {}
@@ -234,33 +276,44 @@ def run_gpu(args):
         for key in ("tests", "hits", "exact", "subbin_queries"):
             b[key] //= max(args.steps, 1)
         b["pair_ms"] /= max(args.steps, 1)
-    # whole-job aggregates (all ranks process the same amount of work)
-    qsegs_job = tot["n_qsegs"] * world
-    tests_job = tot["n_tests"] * world
-    value = qsegs_job / (total_ms / 1e3)
+    btot = {"n_qsegs": 0, "n_tests": 0, "n_hits": 0}
+    for _, st in batch_stats:
+        for key in btot:
+            btot[key] += st["stats"][key]
+    assert btot["n_hits"] == tot["n_hits"], "batched and plain forms disagree"
+    # whole-job aggregates (every rank processes the same amount of work)
+    value = btot["n_qsegs"] * world / (batch_total / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "query segs/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded random walks; stand-in for the paper's Random-1M)",
         "config": {"workload": f"{w.name}: {w.db.n} db segments, {w.queries.n} query segments, "
-                               f"d in {list(w.distances)}, indexes {kinds}, plain per-query-batch "
-                               "search (one ts_search per index and d)",
-                   "l2": "flushed (256 MB write) between timed steps", "form": "plain"},
-        "tests_per_s": tests_job / (total_ms / 1e3),
-        "hits_per_step": tot["n_hits"] // max(args.steps, 1),
-        "gpu_launches": int(launches),
+                               f"d in {list(w.distances)}, indexes {kinds}",
+                   "form": "batched: per index one reusable plan replayed as a CUDA graph, the "
+                           "distances are the requests of one batch",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "tests_per_s": btot["n_tests"] * world / (batch_total / 1e3),
+        "hits_per_step": btot["n_hits"] // max(args.steps, 1),
+        "gpu_launches": int(l2 - l1),
         "clocks": clk,
         "roofline": roofline(tot, pair_ms),
-        "pair_kernel_share": pair_ms / total_ms if total_ms else None,
+        "plain": {"value": tot["n_qsegs"] * world / (plain_total / 1e3), "unit": "query segs/s",
+                  "ms_per_step": plain_total / args.steps,
+                  "tests_per_s": tot["n_tests"] * world / (plain_total / 1e3),
+                  "gpu_launches": int(l1 - l0),
+                  "pair_kernel_share": pair_ms / plain_total if plain_total else None,
+                  "form": "one ts_search per index and d"},
         "breakdown": breakdown,
     }
     if not args.no_e2e:
-        line["e2e"] = run_e2e(args, api, w, indexes, kinds)
+        line["e2e"] = run_e2e(args, api, w, plans, kinds)
     if world > 1:
         dist.barrier()
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w)
+    for pl in plans.values():
+        pl.free()
     for idx in indexes.values():
         idx.free()
     if rank == 0:
@@ -269,33 +322,30 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, api, w, indexes, kinds):
-    """The same step through the C ABI with HOST buffers: H2D of the queries and D2H of every
-    result row inside the timed region."""
+def run_e2e(args, api, w, plans, kinds):
+    """The batched step through the C ABI with HOST buffers: the query columns are staged from
+    host memory and every result row is copied to host memory inside the timed region (wall
+    clock, the stream synchronised on both sides)."""
     import torch
-    stream = torch.cuda.current_stream()
-    h2d = 0
-    d2h = 0
+    reqs = [(w.queries, d, w.t_start, w.t_end) for d in w.distances]
     ms = []
+    h2d = d2h = qsegs = 0
     for s in range(args.steps + 1):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        h2d_s = d2h_s = 0
-        qsegs = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d_s = d2h_s = q_s = 0
         for k in kinds:
-            for d in w.distances:
-                r = api.ts_search(indexes[k], w.queries, d, w.t_start, w.t_end)
-                rows = r.to_host()
-                h2d_s += 8 * 8 * w.queries.n
-                d2h_s += rows["q_idx"].nbytes * 2 + rows["t_in"].nbytes * 2
-                qsegs += r.stats["n_qsegs"]
-                r.free()
-        b.record(stream)
-        b.synchronize()
-        if s > 0:  # first pass is warm-up
-            ms.append(a.elapsed_time(b))
-            h2d, d2h = h2d_s, d2h_s
+            plans[k].run(reqs)
+            st = plans[k].wait()
+            q_s += st["stats"]["n_qsegs"]
+            for r in range(len(reqs)):
+                rows = plans[k].request_to_host(r)
+                d2h_s += sum(v.nbytes for v in rows.values())
+            h2d_s += 8 * 8 * w.queries.n * len(reqs)
+        torch.cuda.synchronize()
+        if s > 0:  # the first pass is warm-up
+            ms.append((time.perf_counter() - t0) * 1e3)
+            h2d, d2h, qsegs = h2d_s, d2h_s, q_s
     t = sum(ms) / 1e3
     return {"value": qsegs * len(ms) / t, "unit": "query segs/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h}

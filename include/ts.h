@@ -250,6 +250,54 @@ ts_status ts_batch_rows(const ts_batch *b, const uint32_t **q_idx, const uint32_
 ts_status ts_batch_copy_rows(const ts_batch *b, uint64_t first, uint64_t count, uint32_t *q_idx,
                              uint32_t *e_idx, double *t_in, double *t_out);
 
+/* ---------------------------------------------------------------------------------------------
+ * Served search: a request loop on a resident index ("D is stored once and queried multiple
+ * times", Sec. 3.1). Requests are submitted from any host thread; a loop thread admits them into
+ * batches while a batch's query and row capacity allow, runs up to max_inflight batches at once
+ * on their own streams (a batch is formed while another runs), splits a batch whose rows
+ * overflow, and hands every request its own result. Every wait is bounded.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct ts_server_params {
+    uint32_t max_inflight;        /* batches on the device at once (>= 1; 2 overlaps batches) */
+    uint32_t max_batch_requests;  /* requests per batch */
+    uint64_t max_batch_queries;   /* query segments per batch (admission capacity) */
+    uint64_t max_batch_rows;      /* result rows per batch (admission capacity) */
+    uint32_t tile_records;        /* as in ts_batch_params */
+    int32_t use_graph;            /* replay each batch plan as a CUDA graph */
+    uint32_t linger_us;           /* how long a partly filled batch waits for more requests */
+    uint32_t reserved;
+} ts_server_params;
+
+typedef struct ts_server ts_server;
+
+/* Host-clock timestamps of a served request, in microseconds since the server started. */
+typedef struct ts_request_timing {
+    double submit_us, start_us, done_us;
+    uint32_t batch_requests;  /* requests in the batch that served it */
+    uint32_t reserved;
+} ts_request_timing;
+
+ts_status ts_server_create(const ts_index *idx, const ts_server_params *params,
+                           ts_server **out);
+
+/* Submit a request: its query segments (host or device arrays; copied before the call returns)
+ * and parameters. *ticket identifies it in ts_server_wait. */
+ts_status ts_server_submit(ts_server *srv, const ts_segments *q, const ts_query_params *qp,
+                           uint64_t *ticket);
+
+/* Wait up to timeout_ms for a request. On success *out receives its result (device rows, release
+ * with ts_free) and *timing its timestamps (may be NULL). TS_ERR_TIMEOUT leaves the request in
+ * place; any other status is the request's own outcome and ends its ticket. */
+ts_status ts_server_wait(ts_server *srv, uint64_t ticket, uint32_t timeout_ms, ts_result **out,
+                         ts_request_timing *timing);
+
+/* Cancel a request that has not started; TS_ERR_INVALID_ARG when it already started or ended. */
+ts_status ts_server_cancel(ts_server *srv, uint64_t ticket);
+
+/* Stop the loop (waits for in-flight batches) and release the server. Requests still queued end
+ * with TS_ERR_CANCELLED. */
+void ts_server_destroy(ts_server *srv);
+
 /* Release a ts_index, ts_result or ts_batch (NULL is a no-op). Waits for the device work of the
  * handle. */
 void ts_free(void *handle);

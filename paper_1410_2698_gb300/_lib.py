@@ -86,6 +86,19 @@ class ts_batch_status(ctypes.Structure):
                 ("overflow", ctypes.c_int32), ("stats", ts_search_stats)]
 
 
+class ts_server_params(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_uint32), ("max_batch_requests", ctypes.c_uint32),
+                ("max_batch_queries", ctypes.c_uint64), ("max_batch_rows", ctypes.c_uint64),
+                ("tile_records", ctypes.c_uint32), ("use_graph", ctypes.c_int32),
+                ("linger_us", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class ts_request_timing(ctypes.Structure):
+    _fields_ = [("submit_us", ctypes.c_double), ("start_us", ctypes.c_double),
+                ("done_us", ctypes.c_double), ("batch_requests", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
 _P = ctypes.c_void_p
 _S = ctypes.c_int
 # name -> (restype, argtypes); every symbol declared in include/ts.h
@@ -119,6 +132,13 @@ SIGNATURES = {
     "ts_batch_rows": (_S, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                            ctypes.POINTER(_P)]),
     "ts_batch_copy_rows": (_S, [_P, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P, _P]),
+    "ts_server_create": (_S, [_P, ctypes.POINTER(ts_server_params), ctypes.POINTER(_P)]),
+    "ts_server_submit": (_S, [_P, ctypes.POINTER(ts_segments), ctypes.POINTER(ts_query_params),
+                              ctypes.POINTER(ctypes.c_uint64)]),
+    "ts_server_wait": (_S, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(_P),
+                            ctypes.POINTER(ts_request_timing)]),
+    "ts_server_cancel": (_S, [_P, ctypes.c_uint64]),
+    "ts_server_destroy": (None, [_P]),
     "ts_search_brute_noalloc": (_S, [ctypes.POINTER(ts_segments), ctypes.POINTER(ts_segments),
                                      ctypes.POINTER(ts_query_params), _P, _P, _P, _P,
                                      ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _P]),

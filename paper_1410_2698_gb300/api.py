@@ -377,3 +377,55 @@ class BatchPlan:
             self.free()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------------------------
+# served search
+# ---------------------------------------------------------------------------------------------
+class Server:
+    """Request loop on a resident index (ts_server_*): submit from any thread, wait per ticket."""
+
+    def __init__(self, index: Index, max_batch_requests=64, max_batch_queries=1 << 20,
+                 max_batch_rows=1 << 26, max_inflight=2, tile_records=0, use_graph=True,
+                 linger_us=200):
+        lib = _lib.load()
+        p = _lib.ts_server_params(int(max_inflight), int(max_batch_requests),
+                                  int(max_batch_queries), int(max_batch_rows),
+                                  int(tile_records), int(use_graph), int(linger_us), 0)
+        h = ctypes.c_void_p()
+        check(lib.ts_server_create(index.handle, ctypes.byref(p), ctypes.byref(h)))
+        self._h = h
+        self.index = index
+
+    def submit(self, queries, d, t_start, t_end, max_results=0) -> int:
+        lib = _lib.load()
+        s, keep = make_segments(queries)
+        qp = _qparams(d, t_start, t_end, max_results)
+        t = ctypes.c_uint64()
+        check(lib.ts_server_submit(self._h, ctypes.byref(s), ctypes.byref(qp), ctypes.byref(t)))
+        del keep
+        return int(t.value)
+
+    def wait(self, ticket, timeout_ms=60000):
+        """Returns (Result, timing dict); raises TsError (status 5 on timeout)."""
+        lib = _lib.load()
+        out = ctypes.c_void_p()
+        tm = _lib.ts_request_timing()
+        check(lib.ts_server_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(out),
+                                 ctypes.byref(tm)))
+        return Result(out, 0), {"submit_us": tm.submit_us, "start_us": tm.start_us,
+                                "done_us": tm.done_us, "batch_requests": int(tm.batch_requests)}
+
+    def cancel(self, ticket):
+        check(_lib.load().ts_server_cancel(self._h, int(ticket)))
+
+    def close(self):
+        if self._h:
+            _lib.load().ts_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "ts_batch.cuh"
+#include "ts_server.cuh"
 
 
 using namespace ts;
@@ -336,6 +337,78 @@ ts_status ts_batch_copy_rows(const ts_batch *h, uint64_t first, uint64_t count, 
     }
     TS_CUDA(cudaStreamSynchronize(s));
     return clear_error(TS_OK);
+}
+
+ts_status ts_server_create(const ts_index *h, const ts_server_params *params, ts_server **out)
+{
+    const Index *ix = reinterpret_cast<const Index *>(h);
+    if (!ix || ix->magic != MAGIC_INDEX || !out) {
+        set_error("ts_server_create: invalid index handle or NULL out");
+        return TS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    return guarded([&]() -> ts_status {
+        Server *s = nullptr;
+        ts_status st = server_create(ix, params, &s);
+        if (st != TS_OK) return st;
+        *out = reinterpret_cast<ts_server *>(s);
+        return clear_error(TS_OK);
+    });
+}
+
+static Server *as_server(ts_server *h)
+{
+    Server *s = reinterpret_cast<Server *>(h);
+    if (!s || *reinterpret_cast<uint32_t *>(s) != MAGIC_SERVER) return nullptr;
+    return s;
+}
+
+ts_status ts_server_submit(ts_server *h, const ts_segments *q, const ts_query_params *qp,
+                           uint64_t *ticket)
+{
+    Server *s = as_server(h);
+    if (!s) {
+        set_error("ts_server_submit: invalid server handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    return guarded([&]() -> ts_status { return server_submit(s, q, qp, ticket); });
+}
+
+ts_status ts_server_wait(ts_server *h, uint64_t ticket, uint32_t timeout_ms, ts_result **out,
+                         ts_request_timing *timing)
+{
+    Server *s = as_server(h);
+    if (!s || !out) {
+        set_error("ts_server_wait: invalid server handle or NULL out");
+        return TS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    return guarded([&]() -> ts_status {
+        SearchOut o;
+        ts_status st = server_wait(s, ticket, timeout_ms, &o, timing);
+        if (st != TS_OK) return st;
+        ts_result *r = new ts_result();
+        r->stream = nullptr;
+        r->out = o;
+        *out = r;
+        return clear_error(TS_OK);
+    });
+}
+
+ts_status ts_server_cancel(ts_server *h, uint64_t ticket)
+{
+    Server *s = as_server(h);
+    if (!s) {
+        set_error("ts_server_cancel: invalid server handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    return server_cancel(s, ticket);
+}
+
+void ts_server_destroy(ts_server *h)
+{
+    Server *s = as_server(h);
+    if (s) server_destroy(s);
 }
 
 uint64_t ts_result_count(const ts_result *r)

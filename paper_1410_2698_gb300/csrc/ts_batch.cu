@@ -304,8 +304,8 @@ ts_status plan_run(BatchPlan *p, uint32_t nreq, const ts_segments *qs, const ts_
     cudaStream_t st = s ? s : p->stream;
     if (p->prm.use_graph) {
         if (!p->exec) {
-            int blocks = 0;
-            (void)blocks;
+            // kernels enqueued during the capture are counted once, for this first replay
+            const unsigned long long before = launch_count();
             TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             ts_status e = enqueue_run(p, st, true);
             cudaGraph_t g = nullptr;
@@ -316,7 +316,10 @@ ts_status plan_run(BatchPlan *p, uint32_t nreq, const ts_segments *qs, const ts_
             }
             if (ce != cudaSuccess) return cuda_status(ce, "cudaStreamEndCapture");
             p->graph = g;
+            p->graph_kernels = launch_count() - before;
             TS_CUDA(cudaGraphInstantiate(&p->exec, g, 0));
+        } else {
+            note_launches(p->graph_kernels);
         }
         TS_CUDA(cudaGraphLaunch(p->exec, st));
     } else {

@@ -45,6 +45,7 @@ struct BatchPlan {
     bool own_stream = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    unsigned long long graph_kernels = 0;  // kernel launches captured in the graph
     bool running = false;
     cudaStream_t last_stream = nullptr;
     uint32_t last_nreq = 0;
@@ -57,6 +58,8 @@ struct RowBlock {
     ts_status alloc(uint64_t n);
     ~RowBlock();
 };
+
+void note_launches(unsigned long long n);
 
 ts_status create_plan(const Index *ix, const ts_batch_params *prm, cudaStream_t s, bool own_rows,
                       BatchPlan **out);
