@@ -276,11 +276,22 @@ def run_gpu(args):
         for key in ("tests", "hits", "exact", "subbin_queries"):
             b[key] //= max(args.steps, 1)
         b["pair_ms"] /= max(args.steps, 1)
-    btot = {"n_qsegs": 0, "n_tests": 0, "n_hits": 0}
+    btot = {"n_qsegs": 0, "n_tests": 0, "n_hits": 0, "n_exact": 0}
+    bpair_ms = 0.0
     for _, st in batch_stats:
         for key in btot:
             btot[key] += st["stats"][key]
+        bpair_ms += st["stats"]["ms_count_pass"] + st["stats"]["ms_write_pass"]
     assert btot["n_hits"] == tot["n_hits"], "batched and plain forms disagree"
+    # roofline of the dominant kernel of the timed form (the batched pair kernel, timed by CUDA
+    # events the plan records around its count and write passes on the launching stream)
+    if bpair_ms > 0:
+        roof = roofline(btot, bpair_ms)
+        roof["timed_form"] = "batched"
+        roof["pair_kernel_share"] = bpair_ms / batch_total if batch_total else None
+    else:
+        roof = roofline(tot, pair_ms)
+        roof["timed_form"] = "plain"
     # whole-job aggregates (every rank processes the same amount of work)
     value = btot["n_qsegs"] * world / (batch_total / 1e3)
     line = {
@@ -297,7 +308,7 @@ def run_gpu(args):
         "hits_per_step": btot["n_hits"] // max(args.steps, 1),
         "gpu_launches": int(l2 - l1),
         "clocks": clk,
-        "roofline": roofline(tot, pair_ms),
+        "roofline": roof,
         "plain": {"value": tot["n_qsegs"] * world / (plain_total / 1e3), "unit": "query segs/s",
                   "ms_per_step": plain_total / args.steps,
                   "tests_per_s": tot["n_tests"] * world / (plain_total / 1e3),

@@ -137,6 +137,8 @@ void destroy_plan(BatchPlan *p)
     if (p->dmem) cudaFree(p->dmem);
     if (p->hmem) cudaFreeHost(p->hmem);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+    for (int e = 0; e < 4; e++)
+        if (p->ev[e]) cudaEventDestroy(p->ev[e]);
     p->magic = 0;
     delete p;
 }
@@ -199,6 +201,7 @@ ts_status create_plan(const Index *ix, const ts_batch_params *prm, cudaStream_t 
     }
     TS_CUDA(cudaMemsetAsync(p->dmem, 0, p->dbytes, p->stream));
     TS_CUDA(cudaStreamSynchronize(p->stream));
+    for (int e = 0; e < 4; e++) TS_CUDA(cudaEventCreate(&p->ev[e]));
     *out = p.release();
     return TS_OK;
 }
@@ -279,9 +282,15 @@ static ts_status enqueue_run(BatchPlan *p, cudaStream_t s, bool write)
         TS_CHECK(pipe_grid_units(p->ix, k.nq, b, k, s));
     }
     TS_CHECK(pipe_group(p->ix, k.nreq, b, k, s));
+    TS_CUDA(cudaEventRecord(p->ev[0], s));
     TS_CHECK(pipe_count(p->ix, p->d_reqs, b, k, s));
+    TS_CUDA(cudaEventRecord(p->ev[1], s));
     TS_CHECK(pipe_scan_rows(b, k, s));
-    if (write) TS_CHECK(pipe_write(p->ix, p->d_reqs, b, k, s));
+    if (write) {
+        TS_CUDA(cudaEventRecord(p->ev[2], s));
+        TS_CHECK(pipe_write(p->ix, p->d_reqs, b, k, s));
+        TS_CUDA(cudaEventRecord(p->ev[3], s));
+    }
     k_req_rows<<<1, 256, 0, s>>>(p->d_run, k.nreq, k.tiles, b, p->d_row0);
     TS_LAUNCHED();
     TS_CUDA(cudaMemcpyAsync(p->h_out->hdr, b.hdr, sizeof(uint32_t) * 8, cudaMemcpyDeviceToHost, s));
@@ -359,6 +368,10 @@ ts_status plan_wait(BatchPlan *p, ts_batch_status *out)
     bs.overflow = (st & DEV_ERR_OVERFLOW) ? 1 : 0;
     fill_stats(p->h_out, &bs.stats);
     bs.stats.n_queries = p->h_run[0];
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) bs.stats.ms_count_pass = ms;
+    if (cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) bs.stats.ms_write_pass = ms;
+    cudaGetLastError();  // an elapsed-time query on events of a graph may be unsupported
     if (out) *out = bs;
     if (st & ~DEV_ERR_OVERFLOW) return read_dev_status(st & ~DEV_ERR_OVERFLOW);
     return TS_OK;

@@ -46,6 +46,7 @@ struct BatchPlan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     unsigned long long graph_kernels = 0;  // kernel launches captured in the graph
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // count pass, write pass bounds
     bool running = false;
     cudaStream_t last_stream = nullptr;
     uint32_t last_nreq = 0;

@@ -145,8 +145,8 @@ static __device__ __forceinline__ void quad_interval(const Quad &k, double *tin,
 // ea = (xmin - d, ymin - d, zmin - d, w0) rounded down; eb = (xmax + d, ..., w1) rounded up.
 static __device__ __forceinline__ bool filter_box(const RecF &r, const float4 &ea, const float4 &eb)
 {
-    return (r.t0 < eb.w) & (r.t1 > ea.w) & (r.xmax >= ea.x) & (r.xmin <= eb.x) &
-           (r.ymax >= ea.y) & (r.ymin <= eb.y) & (r.zmax >= ea.z) & (r.zmin <= eb.z);
+    return (r.t0 < eb.w) && (r.t1 > ea.w) && (r.xmax >= ea.x) && (r.xmin <= eb.x) &&
+           (r.ymax >= ea.y) && (r.ymin <= eb.y) && (r.zmax >= ea.z) && (r.zmin <= eb.z);
 }
 
 // Stage 2: the squared distance between the entry MBB and the query MBB with every subtraction,

@@ -399,7 +399,7 @@ __device__ __forceinline__ uint32_t find_group(const uint64_t *base, uint32_t ng
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(PK_THREADS, 3) k_pair(PairParams P)
+__global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -434,6 +434,7 @@ __global__ void __launch_bounds__(PK_THREADS, 3) k_pair(PairParams P)
         if (lane == 0) t = atomicAdd(&B.counters[PASS], 1u);
         t = __shfl_sync(FULL, t, 0);
         if (t >= ntiles) break;
+        if (PASS == PASS_WRITE && B.tile_off[t + 1] == B.tile_off[t]) continue;  // no rows
         const uint32_t g = find_group(B.tile_base, ngroups, t);
         const uint32_t lt = (uint32_t)(t - B.tile_base[g]);
         const uint32_t nseg = B.g_nseg[g];
@@ -529,43 +530,48 @@ __global__ void __launch_bounds__(PK_THREADS, 3) k_pair(PairParams P)
             pending[st] = false;
             const uint32_t cs = s0 + c * PK_CH;
             const uint32_t cn = min((uint32_t)PK_CH, s1 - cs);
-            // two records per lane: slots lane and lane + 32 of the stage
+            // two records per lane: slots lane and lane + 32 of the stage; an empty slot holds a
+            // record whose time extent is empty, so it never passes the filter
             const bool in0 = (uint32_t)lane < cn, in1 = (uint32_t)lane + 32 < cn;
-            const RecF r0 = W.stage[st][in0 ? lane : 0];
-            const RecF r1 = W.stage[st][in1 ? lane + 32 : 0];
+            RecF r0 = W.stage[st][in0 ? lane : 0];
+            RecF r1 = W.stage[st][in1 ? lane + 32 : 0];
+            if (!in0) r0.t0 = INFINITY;
+            if (!in1) r1.t0 = INFINITY;
             const uint32_t pos0 = cs + lane, pos1 = cs + 32 + lane;
             const uint32_t bend = cs + cn;
-            for (uint32_t mm = 0; mm < count; mm++) {
-                const uint2 rg = W.rng[mm];
-                if (rg.y <= cs || rg.x >= bend) continue;  // warp-uniform
-                const float4 ea = W.ea[mm], eb = W.eb[mm];
-                bool p0 = in0 && filter_box(r0, ea, eb);
-                bool p1 = in1 && filter_box(r1, ea, eb);
-                if (rg.x > cs || rg.y < bend) {  // member covers part of the chunk
-                    p0 = p0 && pos0 >= rg.x && pos0 < rg.y;
-                    p1 = p1 && pos1 >= rg.x && pos1 < rg.y;
-                }
-                if (!__any_sync(FULL, p0 || p1)) continue;
-                p0 = p0 && filter_gap_e(r0, ea, eb, d_dn, d2u);
-                p1 = p1 && filter_gap_e(r1, ea, eb, d_dn, d2u);
-                const unsigned b0 = __ballot_sync(FULL, p0);
-                if (b0) {
-                    if (p0) W.queue[qn + __popc(b0 & lt_mask)] = (mm << 27) | (pos0 - s0);
-                    qn += __popc(b0);
+            // survivors of the box filter go through the gap filter and into the queue
+            auto enqueue = [&](bool p, const float4 &ea, const float4 &eb, const RecF &r,
+                               uint32_t m, uint32_t pos) {
+                p = p && filter_gap_e(r, ea, eb, d_dn, d2u);
+                const unsigned bm = __ballot_sync(FULL, p);
+                if (bm) {
+                    if (p) W.queue[qn + __popc(bm & lt_mask)] = (m << 27) | (pos - s0);
+                    qn += __popc(bm);
                     if (qn >= 32) {
                         __syncwarp();
                         flush(32);
                     }
                 }
-                const unsigned b1 = __ballot_sync(FULL, p1);
-                if (b1) {
-                    if (p1) W.queue[qn + __popc(b1 & lt_mask)] = (mm << 27) | (pos1 - s0);
-                    qn += __popc(b1);
-                    if (qn >= 32) {
-                        __syncwarp();
-                        flush(32);
-                    }
-                }
+            };
+            // two members per iteration; a member whose range misses this chunk gets width 0,
+            // and (pos - lo) < width tests both range ends with one unsigned compare
+            for (uint32_t mm = 0; mm < count; mm += 2) {
+                const uint32_t mb = mm + 1 < count ? mm + 1 : mm;
+                const uint2 ra = W.rng[mm], rb = W.rng[mb];
+                const uint32_t wa = (ra.y > cs && ra.x < bend) ? ra.y - ra.x : 0u;
+                const uint32_t wb = (mb != mm && rb.y > cs && rb.x < bend) ? rb.y - rb.x : 0u;
+                if (!(wa | wb)) continue;  // warp-uniform
+                const float4 eaA = W.ea[mm], ebA = W.eb[mm];
+                const float4 eaB = W.ea[mb], ebB = W.eb[mb];
+                const bool a0 = (pos0 - ra.x) < wa && filter_box(r0, eaA, ebA);
+                const bool a1 = (pos1 - ra.x) < wa && filter_box(r1, eaA, ebA);
+                const bool b0 = (pos0 - rb.x) < wb && filter_box(r0, eaB, ebB);
+                const bool b1 = (pos1 - rb.x) < wb && filter_box(r1, eaB, ebB);
+                if (!__any_sync(FULL, a0 || a1 || b0 || b1)) continue;
+                enqueue(a0, eaA, ebA, r0, mm, pos0);
+                enqueue(a1, eaA, ebA, r1, mm, pos1);
+                enqueue(b0, eaB, ebB, r0, mb, pos0);
+                enqueue(b1, eaB, ebB, r1, mb, pos1);
             }
             __syncwarp();
             if (c + 2 < nch) {

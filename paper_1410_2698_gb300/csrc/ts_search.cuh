@@ -19,8 +19,9 @@ namespace ts {
 constexpr int PK_WARPS = 8;
 constexpr int PK_THREADS = PK_WARPS * 32;
 constexpr int PK_CH = 64;      // records per bulk-copy stage (2 KB): 2 per lane
-constexpr int PK_TILE = 1024;  // records per tile (multiple of PK_CH)
+constexpr int PK_TILE = 256;   // records per tile (multiple of PK_CH)
 constexpr int GROUP = 32;      // units per group
+constexpr int PK_MIN_BLOCKS = 2;  // resident pair-kernel blocks per SM the register budget targets
 
 enum { HDR_U = 0, HDR_G = 1, HDR_T_LO = 2, HDR_T_HI = 3, HDR_N = 4 };
 
