@@ -160,16 +160,19 @@ def roofline(tot, pair_ms):
             "peak_source": "derived: 152 SMs x lanes x 2.07 GHz (FP32), GB300 nominal (FP64)"}
 
 
-def _timed(args, stream, flush, step):
-    """Time args.steps calls of step() with CUDA events on the launching stream; the L2 is
-    flushed (a 256 MB write) before every step, outside the events."""
+def _timed(args, stream, flush, step, steps=None):
+    """Time `steps` calls of step() with CUDA events on the bench stream; the L2 is flushed (a
+    256 MB write, finished before the step starts) before every step, outside the events. A step
+    that runs on other streams synchronises with the host before it returns, so the events
+    bracket all of its work."""
     import torch
     ms = []
-    for _ in range(args.steps):
+    for _ in range(args.steps if steps is None else steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
+        stream.synchronize()
         step()
         b.record(stream)
         b.synchronize()
@@ -199,6 +202,9 @@ def run_gpu(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    # the bench's own launches (plain searches, L2 flush, step events) go to one side stream;
+    # every batch plan runs on a stream of its own
+    torch.cuda.set_stream(torch.cuda.Stream(device=dev))
     w = load_workload(args.workload, rank)
     kinds = [k for k in args.indexes.split(",") if k]
     indexes = {k: api.ts_build_index(w.db, kind=k) for k in kinds}
@@ -226,13 +232,14 @@ def run_gpu(args):
     reqs = [(qdev, d, w.t_start, w.t_end) for d in w.distances]
     plans = {k: api.BatchPlan(indexes[k], max_requests=len(reqs),
                               max_queries=w.queries.n * len(reqs),
-                              max_rows=max(1 << 20, 2 * rows_per_batch[k]), use_graph=True)
+                              max_rows=max(1 << 20, 2 * rows_per_batch[k]), use_graph=True,
+                              stream=0)
              for k in kinds}
     batch_stats = []
 
     def batched_step(collect=None):
         for k in kinds:
-            plans[k].run(reqs)
+            plans[k].run(reqs, stream=0)  # each plan on its own stream: the plans overlap
         for k in kinds:
             st = plans[k].wait()
             if st["overflow"]:
@@ -253,6 +260,16 @@ def run_gpu(args):
     l1 = api.ts_kernel_launches()
     batch_ms = _timed(args, stream, flush, lambda: batched_step(batch_stats))
     l2 = api.ts_kernel_launches()
+    # the pair kernel timed alone: the same plans, one at a time on the bench stream (in the
+    # overlapped step the events of one plan also see the other plans' kernels)
+    alone = []
+
+    def alone_step():
+        for k in kinds:
+            plans[k].run(reqs)
+            alone.append((k, plans[k].wait()))
+
+    alone_ms = _timed(args, stream, flush, alone_step, steps=min(args.steps, 20))
     torch.cuda.synchronize()
     clk = clocks.stop()
     plain_total = _max_over_ranks(float(sum(plain_ms)), world, dev)
@@ -277,18 +294,35 @@ def run_gpu(args):
             b[key] //= max(args.steps, 1)
         b["pair_ms"] /= max(args.steps, 1)
     btot = {"n_qsegs": 0, "n_tests": 0, "n_hits": 0, "n_exact": 0}
-    bpair_ms = 0.0
     for _, st in batch_stats:
         for key in btot:
             btot[key] += st["stats"][key]
-        bpair_ms += st["stats"]["ms_count_pass"] + st["stats"]["ms_write_pass"]
     assert btot["n_hits"] == tot["n_hits"], "batched and plain forms disagree"
-    # roofline of the dominant kernel of the timed form (the batched pair kernel, timed by CUDA
-    # events the plan records around its count and write passes on the launching stream)
-    if bpair_ms > 0:
-        roof = roofline(btot, bpair_ms)
-        roof["timed_form"] = "batched"
-        roof["pair_kernel_share"] = bpair_ms / batch_total if batch_total else None
+    atot = {"n_qsegs": 0, "n_tests": 0, "n_hits": 0, "n_exact": 0}
+    apair_ms = 0.0
+    per_index = {}
+    for k, st in alone:
+        for key in atot:
+            atot[key] += st["stats"][key]
+        ms = st["stats"]["ms_count_pass"] + st["stats"]["ms_write_pass"]
+        apair_ms += ms
+        e = per_index.setdefault(k, {"pair_ms": 0.0, "tests": 0, "tiles": 0, "groups": 0})
+        e["pair_ms"] += ms
+        e["tests"] += st["stats"]["n_tests"]
+        e["tiles"] += st["stats"]["n_tiles"]
+        e["groups"] += st["stats"]["n_groups"]
+    n_alone = max(len(alone_ms), 1)
+    for e in per_index.values():
+        for key in e:
+            e[key] = e[key] / n_alone
+    # roofline of the dominant kernel (the batched pair kernel, count + write passes, timed by
+    # CUDA events the plan records around the passes on its stream, one plan at a time)
+    if apair_ms > 0:
+        roof = roofline(atot, apair_ms)
+        roof["timed_form"] = "batched, one plan at a time (separate loop of the same plans)"
+        roof["pair_kernel_share"] = apair_ms / sum(alone_ms) if alone_ms else None
+        roof["ms_per_step_one_at_a_time"] = sum(alone_ms) / n_alone
+        roof["per_index"] = per_index
     else:
         roof = roofline(tot, pair_ms)
         roof["timed_form"] = "plain"
@@ -346,7 +380,8 @@ def run_e2e(args, api, w, plans, kinds):
         t0 = time.perf_counter()
         h2d_s = d2h_s = q_s = 0
         for k in kinds:
-            plans[k].run(reqs)
+            plans[k].run(reqs, stream=0)  # each plan on its own stream, as in the timed step
+        for k in kinds:
             st = plans[k].wait()
             q_s += st["stats"]["n_qsegs"]
             for r in range(len(reqs)):

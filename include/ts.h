@@ -204,8 +204,8 @@ ts_status ts_search_batch(const ts_index *idx, uint32_t nreq, const ts_segments 
 /* Reusable batch plan with fixed capacities; every run is free of host synchronisation and, with
  * use_graph, is captured once in a CUDA graph and replayed. */
 typedef struct ts_batch_params {
-    uint32_t max_requests;  /* requests per run */
-    uint32_t tile_records;  /* candidate records per work tile, multiple of 64 (0 = 1024) */
+    uint32_t max_requests;  /* requests per run, < 2^24 */
+    uint32_t tile_records;  /* candidate records per work tile, multiple of 64 (0 = 256) */
     uint64_t max_queries;   /* query segments per run, all requests together */
     uint64_t max_rows;      /* result rows per run, all requests together */
     uint64_t max_units;     /* candidate ranges per run (0 = derived) */

@@ -1,0 +1,148 @@
+"""Autotuner for the batched search: bin granularity of the index (temporal bins m, subbins v,
+grid cells g), records per work tile and pair-kernel blocks, chosen by timing a sample batch of
+requests through the C ABI. Results are cached per (workload signature, GPU name) in a JSON file.
+
+The tuner only measures; every candidate runs the same CUDA path (same results, checked by row
+counts), so the choice affects speed only.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+import numpy as np
+
+from . import api
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ts_gb300_autotune.json")
+
+SPACE = {
+    "temporal": {"t_bins": [0.5, 1, 2, 4, 8]},           # multiples of span / longest duration
+    "spatiotemporal": {"t_bins": [1, 4], "sub_bins": [4, 8, 16, 32, 64]},
+    "spatial": {"grid_cells": [10, 25, 50, 100]},
+}
+TILES = [128, 256, 512, 1024]
+
+
+def signature(db, requests, kind) -> str:
+    """Stable key of a workload: database size and extent, request count and sizes, kind."""
+    h = hashlib.sha256()
+    h.update(kind.encode())
+    h.update(np.array([db.n, len(requests)], dtype=np.int64).tobytes())
+    for col in (db.x0, db.y0, db.z0, db.t0, db.t1):
+        h.update(np.array([col.min(), col.max()], dtype=np.float64).tobytes())
+    for q, d, ts, te in requests[:64]:
+        h.update(np.array([q.n if hasattr(q, "n") else 0, d, ts, te], dtype=np.float64).tobytes())
+    return h.hexdigest()[:24]
+
+
+def _gpu_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(0)
+    except Exception:  # pragma: no cover
+        return "unknown"
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, cache):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _time_plan(index, requests, tile, pair_blocks, max_rows, repeats):
+    plan = api.BatchPlan(index, max_requests=len(requests),
+                         max_queries=sum(q.n for q, *_ in requests), max_rows=max_rows,
+                         tile_records=tile, use_graph=True, pair_blocks=pair_blocks)
+    try:
+        plan.run(requests)
+        st = plan.wait()  # warm-up (and graph capture)
+        if st["overflow"]:
+            return None, st
+        best = float("inf")
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            plan.run(requests)
+            st = plan.wait()
+            best = min(best, time.perf_counter() - t0)
+        return best, st
+    finally:
+        plan.free()
+
+
+def tune(db, requests, kind, cache_path=DEFAULT_CACHE, repeats=3, max_rows=1 << 24,
+         index_budget=6, force=False):
+    """Return the best {index params, tile_records, pair_blocks} for `kind` on this workload.
+    requests: list of (queries, d, t_start, t_end) used as the timing sample."""
+    key = f"{signature(db, requests, kind)}|{_gpu_name()}"
+    cache = _load(cache_path)
+    if not force and key in cache:
+        return cache[key]
+    span = float(db.t1.max() - db.t0.min())
+    longest = float((db.t1 - db.t0).max())
+    base = max(1.0, span / max(longest, 1e-300))
+    candidates = []
+    space = SPACE.get(kind, {})
+    if kind == "temporal":
+        for f in space["t_bins"]:
+            candidates.append({"t_bins": int(max(1, min(db.n, round(f * base))))})
+    elif kind == "spatiotemporal":
+        for f in space["t_bins"]:
+            for v in space["sub_bins"]:
+                candidates.append({"t_bins": int(max(1, min(db.n, round(f * base)))),
+                                   "sub_bins": v})
+    elif kind == "spatial":
+        candidates = [{"grid_cells": g} for g in space["grid_cells"]]
+    else:
+        candidates = [{}]
+    candidates = candidates[:max(index_budget, 1)] if len(candidates) > index_budget else candidates
+    trials = []
+    best = None
+    rows = None
+    for params in candidates:
+        idx = api.ts_build_index(db, kind=kind, **params)
+        try:
+            t, st = _time_plan(idx, requests, 256, 0, max_rows, repeats)
+        finally:
+            idx.free()
+        if t is None:
+            continue
+        if rows is None:
+            rows = st["rows"]
+        if st["rows"] != rows:
+            raise RuntimeError("autotune: candidates disagree on the result count")
+        trials.append({"params": params, "s": t})
+        if best is None or t < best[1]:
+            best = (params, t)
+    if best is None:
+        raise RuntimeError("autotune: every candidate overflowed max_rows")
+    idx = api.ts_build_index(db, kind=kind, **best[0])
+    tile_best = (256, 0, best[1])
+    try:
+        for tile in TILES:
+            for pb in (0, 152):  # all resident blocks, or one block per SM
+                t, st = _time_plan(idx, requests, tile, pb, max_rows, repeats)
+                if t is not None:
+                    trials.append({"params": dict(best[0]), "tile_records": tile,
+                                   "pair_blocks": pb, "s": t})
+                    if t < tile_best[2]:
+                        tile_best = (tile, pb, t)
+    finally:
+        idx.free()
+    out = {"index": best[0], "tile_records": tile_best[0], "pair_blocks": tile_best[1],
+           "seconds": tile_best[2], "trials": trials, "rows": rows}
+    cache[key] = out
+    _store(cache_path, cache)
+    return out

@@ -109,6 +109,7 @@ static void layout(BatchPlan *p, Carver &c)
     b.seg_t0 = c.take<uint32_t>(GROUP * k.groups);
     b.ntiles = c.take<uint32_t>(k.groups);
     b.tile_base = c.take<uint64_t>(k.groups + 1);
+    b.tdesc = c.take<uint4>(k.tiles);
     b.tile_hits = c.take<uint32_t>(k.tiles);
     b.tile_off = c.take<uint64_t>(k.tiles + 1);
     if (p->own_rows) {
@@ -148,8 +149,9 @@ ts_status create_plan(const Index *ix, const ts_batch_params *prm, cudaStream_t 
 {
     *out = nullptr;
     if (!prm || prm->max_requests == 0 || prm->max_queries == 0 ||
-        prm->max_queries > 0x7fffffffull || (own_rows && prm->max_rows == 0)) {
-        set_error("batch plan: need max_requests, max_queries (< 2^31) and max_rows > 0");
+        prm->max_requests >= (1u << 24) || prm->max_queries > 0x7fffffffull ||
+        (own_rows && prm->max_rows == 0)) {
+        set_error("batch plan: need max_requests (< 2^24), max_queries (< 2^31) and max_rows > 0");
         return TS_ERR_INVALID_ARG;
     }
     const uint32_t tile = prm->tile_records ? prm->tile_records : (uint32_t)PK_TILE;
@@ -260,6 +262,18 @@ static ts_status stage_requests(BatchPlan *p, uint32_t nreq, const ts_segments *
 
 // Enqueue the run (no host synchronisation; graph-capturable). With write = false the run stops
 // after the scan (one-shot batches size their rows first).
+// Records a timing event; inside a stream capture the event becomes an event-record node of the
+// graph (cudaEventRecordExternal), so that replays time the passes too.
+static cudaError_t record_ev(cudaEvent_t e, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cs);
+    if (ce != cudaSuccess) return ce;
+    return cs == cudaStreamCaptureStatusActive
+               ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+               : cudaEventRecord(e, s);
+}
+
 static ts_status enqueue_run(BatchPlan *p, cudaStream_t s, bool write)
 {
     const PipeCaps &k = p->caps;
@@ -282,14 +296,14 @@ static ts_status enqueue_run(BatchPlan *p, cudaStream_t s, bool write)
         TS_CHECK(pipe_grid_units(p->ix, k.nq, b, k, s));
     }
     TS_CHECK(pipe_group(p->ix, k.nreq, b, k, s));
-    TS_CUDA(cudaEventRecord(p->ev[0], s));
+    TS_CUDA(record_ev(p->ev[0], s));
     TS_CHECK(pipe_count(p->ix, p->d_reqs, b, k, s));
-    TS_CUDA(cudaEventRecord(p->ev[1], s));
+    TS_CUDA(record_ev(p->ev[1], s));
     TS_CHECK(pipe_scan_rows(b, k, s));
     if (write) {
-        TS_CUDA(cudaEventRecord(p->ev[2], s));
+        TS_CUDA(record_ev(p->ev[2], s));
         TS_CHECK(pipe_write(p->ix, p->d_reqs, b, k, s));
-        TS_CUDA(cudaEventRecord(p->ev[3], s));
+        TS_CUDA(record_ev(p->ev[3], s));
     }
     k_req_rows<<<1, 256, 0, s>>>(p->d_run, k.nreq, k.tiles, b, p->d_row0);
     TS_LAUNCHED();
@@ -371,7 +385,7 @@ ts_status plan_wait(BatchPlan *p, ts_batch_status *out)
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) bs.stats.ms_count_pass = ms;
     if (cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) bs.stats.ms_write_pass = ms;
-    cudaGetLastError();  // an elapsed-time query on events of a graph may be unsupported
+    cudaGetLastError();  // a run without a write pass leaves ev[2..3] unrecorded
     if (out) *out = bs;
     if (st & ~DEV_ERR_OVERFLOW) return read_dev_status(st & ~DEV_ERR_OVERFLOW);
     return TS_OK;

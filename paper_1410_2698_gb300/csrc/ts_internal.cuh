@@ -23,8 +23,10 @@ namespace ts {
 // records
 // ---------------------------------------------------------------------------------------------
 struct __align__(16) RecF {
-    float xmin, ymin, zmin, t0;  // t0 rounded toward -inf
-    float xmax, ymax, zmax, t1;  // t1 rounded toward +inf
+    float xmin, xmax;  // each axis as an adjacent (min, max) pair: one 8-byte load per axis
+    float ymin, ymax;
+    float zmin, zmax;
+    float t0, t1;      // t0 rounded toward -inf, t1 toward +inf
 };
 static_assert(sizeof(RecF) == 32, "RecF is 32 bytes");
 

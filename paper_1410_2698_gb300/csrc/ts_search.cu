@@ -89,7 +89,7 @@ struct PrepParams {
     int kind;
     const ReqDesc *reqs;
     uint32_t nreq;
-    int lo_bits;
+    KeyFmt kf;
     // index
     uint64_t n;
     uint32_t m;
@@ -104,9 +104,14 @@ struct PrepParams {
     PipeBufs b;
 };
 
-__device__ __forceinline__ uint64_t unit_key(uint32_t r, uint32_t sel, uint32_t lo, int lo_bits)
+// Sort key of a unit: (request, array, range start). Only the top KEY_LO_BITS bits of the start
+// are kept: the sort gathers units with nearby ranges into groups, and the groups order their
+// members exactly before merging their ranges.
+__device__ __forceinline__ uint64_t unit_key(uint32_t r, uint32_t sel, uint32_t lo, KeyFmt f)
 {
-    return ((uint64_t)r << (3 + lo_bits)) | ((uint64_t)sel << lo_bits) | (uint64_t)lo;
+    const uint32_t sb = f.sel_bits ? (sel & ((1u << f.sel_bits) - 1u)) : 0u;
+    return ((uint64_t)r << (f.sel_bits + f.lo_bits)) | ((uint64_t)sb << f.lo_bits) |
+           (uint64_t)(lo >> f.lo_shift);
 }
 
 __global__ void k_qprep(PrepParams P)
@@ -225,7 +230,7 @@ __global__ void k_qprep(PrepParams P)
             P.b.u_lo[i] = lo;
             P.b.u_hi[i] = hi;
             P.b.u_sel[i] = sel;
-            P.b.keys[i] = unit ? unit_key(r, sel, lo, P.lo_bits) : ~0ull;
+            P.b.keys[i] = unit ? unit_key(r, sel, lo, P.kf) : ~0ull;
             P.b.vals[i] = (uint32_t)i;
             if (unit) atomicAdd(&P.b.req_units[r], 1u);
         }
@@ -242,7 +247,7 @@ __global__ void k_qprep(PrepParams P)
 
 // Grid index: one unit per (cx, cy) of a query's cell box, covering cells cz_a..cz_b (a z-run
 // of the row-major cell order, contiguous in the lookup array).
-__global__ void k_grid_units(uint64_t nqcap, uint64_t ucap, int lo_bits, uint32_t g,
+__global__ void k_grid_units(uint64_t nqcap, uint64_t ucap, KeyFmt kf, uint32_t g,
                              const uint32_t *g_off, PipeBufs b)
 {
     const uint64_t nq = b.run ? min((uint64_t)b.run[0], nqcap) : nqcap;
@@ -268,7 +273,7 @@ __global__ void k_grid_units(uint64_t nqcap, uint64_t ucap, int lo_bits, uint32_
                 b.u_lo[u] = lo;
                 b.u_hi[u] = hi;
                 b.u_sel[u] = SEL_GRID;
-                b.keys[u] = hi > lo ? unit_key(r, SEL_GRID, lo, lo_bits) : ~0ull;
+                b.keys[u] = hi > lo ? unit_key(r, SEL_GRID, lo, kf) : ~0ull;
                 b.vals[u] = u;
                 nvalid += hi > lo;
             }
@@ -320,15 +325,29 @@ __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, PipeBu
         const uint32_t end = min(first + GROUP, b.ustart[r] + b.req_units[r]);
         b.g_first[g] = first;
         b.g_count[g] = end - first;
-        // merge the members' ranges (sorted by array, then start) into disjoint segments
+        // order the members by (array, start), then merge their ranges into disjoint segments
+        uint32_t ms[GROUP], ml[GROUP], mh[GROUP];
+        const uint32_t n = end - first;
+        for (uint32_t p = 0; p < n; p++) {
+            const uint32_t u = b.vals[first + p];
+            uint32_t s = b.u_sel[u], l = b.u_lo[u], h = b.u_hi[u];
+            uint32_t j = p;
+            for (; j > 0 && (ms[j - 1] > s || (ms[j - 1] == s && ml[j - 1] > l)); j--) {
+                ms[j] = ms[j - 1];
+                ml[j] = ml[j - 1];
+                mh[j] = mh[j - 1];
+            }
+            ms[j] = s;
+            ml[j] = l;
+            mh[j] = h;
+        }
         uint32_t nseg = 0, tiles = 0;
         uint32_t cs = 0, clo = 0, chi = 0;
         bool open = false;
         uint32_t *slo = b.seg_lo + (uint64_t)g * GROUP, *shi = b.seg_hi + (uint64_t)g * GROUP;
         uint32_t *ssel = b.seg_sel + (uint64_t)g * GROUP, *st0 = b.seg_t0 + (uint64_t)g * GROUP;
-        for (uint32_t p = first; p < end; p++) {
-            const uint32_t u = b.vals[p];
-            const uint32_t s = b.u_sel[u], ul = b.u_lo[u], uh = b.u_hi[u];
+        for (uint32_t p = 0; p < n; p++) {
+            const uint32_t s = ms[p], ul = ml[p], uh = mh[p];
             if (open && s == cs && ul <= chi) {
                 chi = max(chi, uh);
                 continue;
@@ -358,7 +377,38 @@ __global__ void k_hdr(uint64_t gcap, uint64_t tcap, PipeBufs b)
     b.hdr[HDR_T_HI] = (uint32_t)(T >> 32);
     b.stats[ST_GROUPS] = b.hdr[HDR_G];
     b.stats[ST_TILES] = T;
-    if (T > tcap) atomicOr(b.status, DEV_ERR_OVERFLOW);
+    if (T > tcap || T > PK_MAX_TILES) atomicOr(b.status, DEV_ERR_OVERFLOW);
+}
+
+// One descriptor per tile (a warp per group, lanes over the tiles of each merged segment), so
+// that the pair kernel finds a tile's group, records and request with a single load.
+__global__ void k_tile_desc(uint64_t gcap, uint64_t tcap, uint32_t tile, PipeBufs b)
+{
+    const uint32_t G = b.hdr[HDR_G];
+    const uint64_t T = (uint64_t)b.hdr[HDR_T_LO] | ((uint64_t)b.hdr[HDR_T_HI] << 32);
+    if (T > tcap || T > PK_MAX_TILES) return;  // overflow flagged by the header kernel
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G && g < gcap;
+         g += warps) {
+        const uint32_t first = b.g_first[g], count = b.g_count[g];
+        if (!count) continue;
+        const uint32_t r = b.qreq[b.u_q[b.vals[first]]];
+        const uint64_t base = b.tile_base[g];
+        const uint32_t nseg = b.g_nseg[g];
+        for (uint32_t k = 0; k < nseg; k++) {
+            const uint64_t o = (uint64_t)g * GROUP + k;
+            const uint32_t lo = b.seg_lo[o], hi = b.seg_hi[o], sel = b.seg_sel[o];
+            const uint32_t t0 = b.seg_t0[o];
+            const uint32_t n = (hi - lo + tile - 1) / tile;
+            for (uint32_t j = lane; j < n; j += 32) {
+                const uint32_t s0 = lo + j * tile;
+                const uint32_t s1 = min(hi, s0 + tile);
+                b.tdesc[base + t0 + j] =
+                    make_uint4(first, s0, s1, sel | ((count - 1) << 3) | (r << 8));
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -366,11 +416,12 @@ __global__ void k_hdr(uint64_t gcap, uint64_t tcap, PipeBufs b)
 // ---------------------------------------------------------------------------------------------
 struct __align__(16) WarpSmem {
     RecF stage[2][PK_CH];
-    float4 ea[GROUP], eb[GROUP];
-    uint2 rng[GROUP];
-    uint32_t qg[GROUP];   // query index in the batch
-    uint32_t ql[GROUP];   // query index within its request
-    uint32_t queue[64];
+    float4 ea[GROUP], eb[GROUP];  // members' expanded boxes (sparse sweep)
+    uint2 rng[GROUP];             // members' own ranges (sorted positions)
+    uint32_t qg[GROUP];           // members' query index in the batch
+    // exact-test queue, first in first out, carried from tile to tile: query index in the batch,
+    // entry position in its sorted array, tile | sel << 29, query index within its request
+    uint32_t q_qi[PK_QUEUE], q_pos[PK_QUEUE], q_tile[PK_QUEUE], q_ql[PK_QUEUE];
     unsigned long long bar[2];
 };
 
@@ -388,16 +439,13 @@ struct PairParams {
     uint32_t tile;      // records per tile
 };
 
-__device__ __forceinline__ uint32_t find_group(const uint64_t *base, uint32_t ng, uint64_t t)
-{
-    uint32_t lo = 0, hi = ng;  // first g with base[g] > t, minus one
-    while (lo < hi) {
-        uint32_t mid = lo + (hi - lo) / 2;
-        if (base[mid] <= t) lo = mid + 1; else hi = mid;
-    }
-    return lo - 1;
-}
-
+// Persistent pair kernel. Warps take tiles (a group of up to 32 query units and up to `tile`
+// consecutive entries of one sorted array) from a device counter. Entry records stream through
+// a two-stage shared-memory buffer filled by 1-D bulk copies. The conservative FP32 filters pick
+// the candidates of the exact FP64 test; those wait in a per-warp queue that is carried across
+// tiles and drained 32 at a time, so that the FP64 instructions run on full warps.
+// Count pass: hits per tile. Write pass: the rows of every tile with hits, at its offset from the
+// scan, in queue order (the same order in both passes, so the offsets match).
 template <int PASS>
 __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P)
 {
@@ -419,56 +467,98 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
     bool pending[2] = {false, false};
     bool abort = false;
 
-    const uint32_t ngroups = B.hdr[HDR_G];
     uint64_t ntiles = (uint64_t)B.hdr[HDR_T_LO] | ((uint64_t)B.hdr[HDR_T_HI] << 32);
-    if (ntiles > P.tcap) ntiles = 0;  // overflow already flagged
+    if (ntiles > P.tcap || ntiles > PK_MAX_TILES) ntiles = 0;  // overflow already flagged
     if (PASS == PASS_WRITE && ntiles && B.tile_off[ntiles] > P.rows_cap) {
         // more rows than the output holds: write none (the caller sees the exact count)
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, DEV_ERR_OVERFLOW);
         ntiles = 0;
     }
     unsigned long long acc_tests = 0, acc_exact = 0, acc_hits = 0;
+    uint32_t qn = 0;                            // queued candidates (warp-uniform)
+    uint32_t wt_cur = 0xffffffffu, wt_cnt = 0;  // write pass: last tile with rows, rows so far
 
-    while (!abort) {
-        uint64_t t = 0;
-        if (lane == 0) t = atomicAdd(&B.counters[PASS], 1u);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= ntiles) break;
-        if (PASS == PASS_WRITE && B.tile_off[t + 1] == B.tile_off[t]) continue;  // no rows
-        const uint32_t g = find_group(B.tile_base, ngroups, t);
-        const uint32_t lt = (uint32_t)(t - B.tile_base[g]);
-        const uint32_t nseg = B.g_nseg[g];
-        const uint32_t *st0 = B.seg_t0 + (uint64_t)g * GROUP;
-        uint32_t k = 0;
-        while (k + 1 < nseg && st0[k + 1] <= lt) k++;
-        const uint32_t sel = B.seg_sel[(uint64_t)g * GROUP + k];
-        const uint32_t s0 = B.seg_lo[(uint64_t)g * GROUP + k] + (lt - st0[k]) * P.tile;
-        const uint32_t s1 = min(B.seg_hi[(uint64_t)g * GROUP + k], s0 + P.tile);
-        const uint32_t first = B.g_first[g], count = B.g_count[g];
-        const RecF *recs = P.rec[sel];
-        const uint32_t *ids = P.ids[sel];
-
-        // members of the group (one per lane)
-        if ((uint32_t)lane < count) {
-            const uint32_t u = B.vals[first + lane];
-            const uint32_t qi = B.u_q[u];
-            uint32_t lo = B.u_lo[u], hi = B.u_hi[u];
-            if (B.u_sel[u] != sel) lo = hi = 0;
-            W.rng[lane] = make_uint2(lo, hi);
-            W.qg[lane] = qi;
-            W.ql[lane] = qi - P.reqs[B.qreq[qi]].q_first;
-            W.ea[lane] = B.qf[2 * (uint64_t)qi + 0];
-            W.eb[lane] = B.qf[2 * (uint64_t)qi + 1];
-            if (PASS == PASS_COUNT) {
-                const uint32_t a = max(lo, s0), bnd = min(hi, s1);
-                acc_tests += bnd > a ? bnd - a : 0u;
-            }
+    // Exact test of the oldest nflush queued candidates, one per lane.
+    auto flush = [&](uint32_t nflush) {
+        uint32_t qi = 0, pos = 0, tw = 0xffffffffu, ql = 0;
+        if ((uint32_t)lane < nflush) {
+            qi = W.q_qi[lane];
+            pos = W.q_pos[lane];
+            tw = W.q_tile[lane];
+            if (PASS == PASS_WRITE) ql = W.q_ql[lane];
         }
         __syncwarp();
-        // a group's members belong to one request: its d bounds for the gap filter
-        const ReqDesc &RQ = P.reqs[B.qreq[W.qg[0]]];
-        const float d_dn = RQ.d_dn, d2u = RQ.d2u;
+        if (qn > nflush && (uint32_t)lane < qn - nflush) {
+            const uint32_t j = nflush + lane;
+            W.q_qi[lane] = W.q_qi[j];
+            W.q_pos[lane] = W.q_pos[j];
+            W.q_tile[lane] = W.q_tile[j];
+            if (PASS == PASS_WRITE) W.q_ql[lane] = W.q_ql[j];
+        }
+        __syncwarp();
+        qn -= nflush;
+        acc_exact += nflush;
+        bool h = false;
+        double tin = 0.0, tout = 0.0;
+        uint32_t eid = 0;
+        const uint32_t tile = tw & PK_MAX_TILES;
+        if ((uint32_t)lane < nflush) {
+            const uint32_t *ids = P.ids[tw >> 29];
+            eid = ids ? ids[pos] : pos;
+            const SegD e = P.seg[eid];
+            const QueryD q = B.qd[qi];
+            Quad qd;
+            if (pair_quad(q, e, q.pad, qd) && quad_hit(qd)) {
+                h = true;
+                if (PASS == PASS_WRITE) quad_interval(qd, &tin, &tout);
+            }
+        }
+        const unsigned hm = __ballot_sync(FULL, h);
+        if (!hm) return;
+        acc_hits += __popc(hm);
+        // hits of the same tile (the queue holds a tile's candidates contiguously, tiles in the
+        // order this warp took them)
+        const unsigned mine = hm & __match_any_sync(FULL, h ? tile : 0xffffffffu);
+        if (PASS == PASS_COUNT) {
+            if (h && (mine & lt_mask) == 0) atomicAdd(&B.tile_hits[tile], (uint32_t)__popc(mine));
+        } else {
+            if (h) {
+                const uint64_t o = B.tile_off[tile] + (tile == wt_cur ? wt_cnt : 0u) +
+                                   __popc(mine & lt_mask);
+                if (o < B.tile_off[tile + 1]) {
+                    B.out_q[o] = ql;
+                    B.out_e[o] = P.orig[eid];
+                    B.out_tin[o] = tin;
+                    B.out_tout[o] = tout;
+                } else {
+                    atomicOr(B.status, DEV_ERR_INTERNAL);  // the passes disagree
+                }
+            }
+            const int last = 31 - __clz(hm);
+            const uint32_t last_tile = __shfl_sync(FULL, tile, last);
+            const uint32_t last_n = __popc(__shfl_sync(FULL, mine, last));
+            wt_cnt = (last_tile == wt_cur ? wt_cnt : 0u) + last_n;
+            wt_cur = last_tile;
+        }
+    };
 
+    // tiles are taken from a device counter; the next index is fetched while a tile is swept
+    uint64_t t = 0;
+    if (lane == 0) t = atomicAdd(&B.counters[PASS], 1u);
+    t = __shfl_sync(FULL, t, 0);
+    while (!abort && t < ntiles) {
+        uint64_t t_next = 0;
+        if (lane == 0) t_next = atomicAdd(&B.counters[PASS], 1u);
+        if (PASS == PASS_WRITE && B.tile_hits[t] == 0) {  // no rows in this tile
+            t = __shfl_sync(FULL, t_next, 0);
+            continue;
+        }
+        const uint4 D = B.tdesc[t];
+        const uint32_t first = D.x, s0 = D.y, s1 = D.z;
+        const uint32_t sel = D.w & 7u, count = ((D.w >> 3) & 31u) + 1u, req = D.w >> 8;
+        const uint32_t tw = (uint32_t)t | (sel << 29);
+        const RecF *recs = P.rec[sel];
+        // the first two chunks of records are in flight while the members are loaded
         const uint32_t nrec = s1 - s0;
         const uint32_t nch = (nrec + PK_CH - 1) / PK_CH;
         if (lane == 0) {
@@ -480,44 +570,56 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         }
         pending[0] = nch > 0;
         pending[1] = nch > 1;
+        // a group's members belong to one request: its d bounds for the gap filter
+        const ReqDesc &RQ = P.reqs[req];
+        const float d_dn = RQ.d_dn, d2u = RQ.d2u;
+        const uint32_t q_first = RQ.q_first;
 
-        uint32_t qn = 0, hits = 0;
-        const uint64_t wbase = PASS == PASS_WRITE ? B.tile_off[t] : 0;
-        const uint64_t wend = PASS == PASS_WRITE ? B.tile_off[t + 1] : 0;
+        // members of the group: one per lane, their expanded boxes and ranges in registers
+        uint32_t lo = 0, hi = 0, myq = 0;
+        float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
+        if ((uint32_t)lane < count) {
+            const uint32_t u = B.vals[first + lane];
+            myq = B.u_q[u];
+            lo = B.u_lo[u];
+            hi = B.u_hi[u];
+            if (B.u_sel[u] != sel) lo = hi = 0;
+            W.qg[lane] = myq;
+            ea = B.qf[2 * (uint64_t)myq + 0];
+            eb = B.qf[2 * (uint64_t)myq + 1];
+            W.ea[lane] = ea;
+            W.eb[lane] = eb;
+            W.rng[lane] = make_uint2(lo, hi);
+            if (PASS == PASS_COUNT) {
+                const uint32_t a = max(lo, s0), bnd = min(hi, s1);
+                acc_tests += bnd > a ? bnd - a : 0u;
+            }
+        }
+        __syncwarp();
+        // the axis of the stage-1 sweep, the one on which the array's entries are least likely
+        // to meet the query: time for grid cells (a cell holds entries of every time), y for an
+        // X subbin (its entries overlap the query in x by construction), x otherwise
+        const int dim = sel == SEL_GRID ? 3 : (sel == SEL_X ? 1 : 0);
+        const float fa = dim == 3 ? ea.w : (dim == 1 ? ea.y : ea.x);
+        const float fb = dim == 3 ? eb.w : (dim == 1 ? eb.y : eb.x);
 
-        auto flush = [&](uint32_t nflush) {
-            const uint32_t item = (uint32_t)lane < nflush ? W.queue[lane] : 0u;
-            __syncwarp();
-            if (qn > nflush && (uint32_t)lane < qn - nflush) W.queue[lane] = W.queue[nflush + lane];
-            __syncwarp();
-            bool h = false;
-            double tin = 0.0, tout = 0.0;
-            const uint32_t m = item >> 27;
-            uint32_t eid = 0;
-            if ((uint32_t)lane < nflush) {
-                const uint32_t pos = s0 + (item & 0x07ffffffu);
-                eid = ids ? ids[pos] : pos;
-                const SegD e = P.seg[eid];
-                const QueryD q = B.qd[W.qg[m]];
-                Quad qd;
-                if (pair_quad(q, e, q.pad, qd) && quad_hit(qd)) {
-                    h = true;
-                    if (PASS == PASS_WRITE) quad_interval(qd, &tin, &tout);
+        // a candidate that passed the filters joins the exact-test queue
+        auto enqueue = [&](bool p, uint32_t qi, uint32_t pos) {
+            const unsigned bm = __ballot_sync(FULL, p);
+            if (bm) {
+                if (p) {
+                    const uint32_t j = qn + __popc(bm & lt_mask);
+                    W.q_qi[j] = qi;
+                    W.q_pos[j] = pos;
+                    W.q_tile[j] = tw;
+                    if (PASS == PASS_WRITE) W.q_ql[j] = qi - q_first;
+                }
+                qn += __popc(bm);
+                if (qn >= 32) {
+                    __syncwarp();
+                    flush(32);
                 }
             }
-            const unsigned hm = __ballot_sync(FULL, h);
-            if (PASS == PASS_WRITE && h) {
-                const uint64_t o = wbase + hits + __popc(hm & lt_mask);
-                if (o < wend) {
-                    B.out_q[o] = W.ql[m];
-                    B.out_e[o] = P.orig[eid];
-                    B.out_tin[o] = tin;
-                    B.out_tout[o] = tout;
-                }
-            }
-            hits += __popc(hm);
-            acc_exact += nflush;
-            qn -= nflush;
         };
 
         for (uint32_t c = 0; c < nch && !abort; c++) {
@@ -530,48 +632,73 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             pending[st] = false;
             const uint32_t cs = s0 + c * PK_CH;
             const uint32_t cn = min((uint32_t)PK_CH, s1 - cs);
-            // two records per lane: slots lane and lane + 32 of the stage; an empty slot holds a
-            // record whose time extent is empty, so it never passes the filter
-            const bool in0 = (uint32_t)lane < cn, in1 = (uint32_t)lane + 32 < cn;
-            RecF r0 = W.stage[st][in0 ? lane : 0];
-            RecF r1 = W.stage[st][in1 ? lane + 32 : 0];
-            if (!in0) r0.t0 = INFINITY;
-            if (!in1) r1.t0 = INFINITY;
-            const uint32_t pos0 = cs + lane, pos1 = cs + 32 + lane;
-            const uint32_t bend = cs + cn;
-            // survivors of the box filter go through the gap filter and into the queue
-            auto enqueue = [&](bool p, const float4 &ea, const float4 &eb, const RecF &r,
-                               uint32_t m, uint32_t pos) {
-                p = p && filter_gap_e(r, ea, eb, d_dn, d2u);
-                const unsigned bm = __ballot_sync(FULL, p);
-                if (bm) {
-                    if (p) W.queue[qn + __popc(bm & lt_mask)] = (m << 27) | (pos - s0);
-                    qn += __popc(bm);
-                    if (qn >= 32) {
-                        __syncwarp();
-                        flush(32);
-                    }
+            // this lane's own range within the chunk, as bits of the 64 stage slots
+            const uint32_t va = max(lo, cs), vb = min(hi, cs + cn);
+            uint32_t v0 = 0u, v1 = 0u;
+            if (vb > va) {
+                const uint32_t x = va - cs, y = vb - cs;  // 0 <= x < y <= 64
+                v0 = (y >= 32 ? FULL : ((1u << y) - 1u)) & (x >= 32 ? 0u : (FULL << x));
+                v1 = y <= 32 ? 0u : ((y >= 64 ? FULL : ((1u << (y - 32)) - 1u)) &
+                                     (x <= 32 ? FULL : (FULL << (x - 32))));
+            }
+            uint32_t m0 = 0u, m1 = 0u;
+            const unsigned act = __ballot_sync(FULL, (v0 | v1) != 0u);
+            if (__popc(act) <= PK_SPARSE) {
+                // few members meet this chunk: one lane per slot (slots lane and lane + 32), the
+                // members that meet the chunk in turn, their boxes read as broadcasts
+                const bool in0 = (uint32_t)lane < cn, in1 = (uint32_t)lane + 32 < cn;
+                RecF r0 = W.stage[st][lane];
+                RecF r1 = W.stage[st][lane + 32];
+                if (!in0) r0.t0 = INFINITY;  // a slot past the chunk never passes the filter
+                if (!in1) r1.t0 = INFINITY;
+                const uint32_t pos0 = cs + lane, pos1 = cs + 32 + lane;
+                for (unsigned rem = act; rem; rem &= rem - 1u) {
+                    const uint32_t m = __ffs(rem) - 1;
+                    const uint2 rg = W.rng[m];
+                    const float4 mea = W.ea[m], meb = W.eb[m];
+                    const uint32_t mq = W.qg[m];
+                    const uint32_t w = rg.y - rg.x;
+                    bool p0 = (pos0 - rg.x) < w && filter_box(r0, mea, meb);
+                    bool p1 = (pos1 - rg.x) < w && filter_box(r1, mea, meb);
+                    p0 = p0 && filter_gap_e(r0, mea, meb, d_dn, d2u);
+                    p1 = p1 && filter_gap_e(r1, mea, meb, d_dn, d2u);
+                    enqueue(p0, mq, pos0);
+                    enqueue(p1, mq, pos1);
                 }
-            };
-            // two members per iteration; a member whose range misses this chunk gets width 0,
-            // and (pos - lo) < width tests both range ends with one unsigned compare
-            for (uint32_t mm = 0; mm < count; mm += 2) {
-                const uint32_t mb = mm + 1 < count ? mm + 1 : mm;
-                const uint2 ra = W.rng[mm], rb = W.rng[mb];
-                const uint32_t wa = (ra.y > cs && ra.x < bend) ? ra.y - ra.x : 0u;
-                const uint32_t wb = (mb != mm && rb.y > cs && rb.x < bend) ? rb.y - rb.x : 0u;
-                if (!(wa | wb)) continue;  // warp-uniform
-                const float4 eaA = W.ea[mm], ebA = W.eb[mm];
-                const float4 eaB = W.ea[mb], ebB = W.eb[mb];
-                const bool a0 = (pos0 - ra.x) < wa && filter_box(r0, eaA, ebA);
-                const bool a1 = (pos1 - ra.x) < wa && filter_box(r1, eaA, ebA);
-                const bool b0 = (pos0 - rb.x) < wb && filter_box(r0, eaB, ebB);
-                const bool b1 = (pos1 - rb.x) < wb && filter_box(r1, eaB, ebB);
-                if (!__any_sync(FULL, a0 || a1 || b0 || b1)) continue;
-                enqueue(a0, eaA, ebA, r0, mm, pos0);
-                enqueue(a1, eaA, ebA, r1, mm, pos1);
-                enqueue(b0, eaB, ebB, r0, mb, pos0);
-                enqueue(b1, eaB, ebB, r1, mb, pos1);
+            } else {
+                // stage 1: one axis of every slot against every member (slot i is read at a
+                // warp-uniform address, a shared-memory broadcast); bit i is set when the axis
+                // extents overlap. Four independent accumulators per half keep the OR chains
+                // short.
+                const float2 *ax = reinterpret_cast<const float2 *>(&W.stage[st][0]) + dim;
+                uint32_t a[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+                for (int i = 0; i < 64; i++) {
+                    const float2 v = ax[4 * i];
+                    if ((v.y >= fa) & (v.x <= fb)) a[(i >> 5) * 4 + (i & 3)] |= 1u << (i & 31);
+                }
+                m0 = ((a[0] | a[1]) | (a[2] | a[3])) & v0;
+                m1 = ((a[4] | a[5]) | (a[6] | a[7])) & v1;
+            }
+            // stage 2: the survivors, one per lane per round, through the full box and gap
+            // filters and into the exact-test queue
+            for (;;) {
+                const bool have = (m0 | m1) != 0u;
+                if (!__any_sync(FULL, have)) break;
+                bool p = false;
+                uint32_t i = 0;
+                if (have) {
+                    if (m0) {
+                        i = __ffs(m0) - 1;
+                        m0 &= m0 - 1u;
+                    } else {
+                        i = 31 + __ffs(m1);
+                        m1 &= m1 - 1u;
+                    }
+                    const RecF r = W.stage[st][i];
+                    p = filter_box(r, ea, eb) && filter_gap_e(r, ea, eb, d_dn, d2u);
+                }
+                enqueue(p, myq, cs + i);
             }
             __syncwarp();
             if (c + 2 < nch) {
@@ -583,18 +710,12 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 pending[st] = true;
             }
         }
-        if (abort) break;
-        if (qn) {
-            __syncwarp();
-            flush(qn);
-        }
-        if (PASS == PASS_COUNT) {
-            if (lane == 0) B.tile_hits[t] = hits;
-            acc_hits += hits;
-        } else {
-            if (lane == 0 && wbase + hits != wend) atomicOr(B.status, DEV_ERR_INTERNAL);
-        }
         __syncwarp();
+        t = __shfl_sync(FULL, t_next, 0);
+    }
+    if (!abort && qn) {
+        __syncwarp();
+        flush(qn);
     }
     if (abort) {
         if (lane == 0) atomicOr(B.status, DEV_ERR_TIMEOUT);
@@ -703,13 +824,17 @@ int bits_for(uint64_t v)
 // ---------------------------------------------------------------------------------------------
 // pipeline stages
 // ---------------------------------------------------------------------------------------------
-int key_bits(const Index *ix, uint32_t nreq)
+KeyFmt key_fmt(const Index *ix)
 {
-    (void)nreq;
     uint64_t maxlen = ix->n;
     for (int d = 0; d < 3; d++) maxlen = std::max<uint64_t>(maxlen, ix->st_len[d]);
     maxlen = std::max<uint64_t>(maxlen, ix->g_len);
-    return bits_for(maxlen);  // bits of a range start
+    KeyFmt f;
+    const int full = bits_for(maxlen);  // bits of a range start
+    f.lo_bits = std::min(full, KEY_LO_BITS);
+    f.lo_shift = full - f.lo_bits;
+    f.sel_bits = ix->kind == TS_INDEX_SPATIOTEMPORAL ? 2 : 0;  // X, Y, Z or T
+    return f;
 }
 
 void fill_req(ReqDesc &r, const ts_query_params *qp, uint32_t q_first, uint32_t q_count)
@@ -741,7 +866,7 @@ ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq
     P.kind = ix->kind;
     P.reqs = reqs;
     P.nreq = nreq;
-    P.lo_bits = key_bits(ix, nreq);
+    P.kf = key_fmt(ix);
     P.n = ix->n;
     P.m = ix->m;
     P.tmin = ix->tmin;
@@ -773,7 +898,7 @@ ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const
 {
     (void)c;
     if (!nq) return TS_OK;
-    k_grid_units<<<nblk(nq), TPB, 0, s>>>(nq, c.units, key_bits(ix, 1), ix->g, ix->g_off, b);
+    k_grid_units<<<nblk(nq), TPB, 0, s>>>(nq, c.units, key_fmt(ix), ix->g, ix->g_off, b);
     TS_LAUNCHED();
     return TS_OK;
 }
@@ -781,7 +906,9 @@ ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const
 ts_status pipe_group(const Index *ix, uint32_t nreq, const PipeBufs &b, const PipeCaps &c,
                      cudaStream_t s)
 {
-    const int bits = key_bits(ix, nreq) + 3 + bits_for(nreq > 1 ? nreq - 1 : 0);
+    // one bit above the key fields: a unit without candidates has key ~0 and sorts last
+    const KeyFmt f = key_fmt(ix);
+    const int bits = f.lo_bits + f.sel_bits + bits_for(nreq > 1 ? nreq - 1 : 0) + 1;
     TS_CHECK(radix_sort_u64(b.keys, b.vals, c.units, bits, s));
     k_req_scan<<<1, 32, 0, s>>>(nreq, b);
     TS_LAUNCHED();
@@ -803,6 +930,9 @@ ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
     fill_pair_params(P, ix, reqs, b, c);
     if (c.tiles) {
         TS_CUDA(cudaMemsetAsync(b.tile_hits, 0, sizeof(uint32_t) * c.tiles, s));
+        const unsigned dblk = (unsigned)std::min<uint64_t>((c.groups * 32 + TPB - 1) / TPB, 152 * 16);
+        k_tile_desc<<<dblk, TPB, 0, s>>>(c.groups, c.tiles, c.tile, b);
+        TS_LAUNCHED();
         k_pair<PASS_COUNT><<<blocks, PK_THREADS, sizeof(WarpSmem) * PK_WARPS, s>>>(P);
         TS_LAUNCHED();
     }
@@ -896,7 +1026,7 @@ namespace {
 // Work buffers of a plain search, allocated stage by stage at their exact sizes.
 struct PlainWork {
     DevBuf qd, qf, qreq, qcell, qnu, quoff, u_q, u_lo, u_hi, u_sel, keys, vals, req, groups, segs,
-        ntiles, tile_base, tiles, tile_off, ctl, reqdesc;
+        ntiles, tile_base, tiles, tdesc, tile_off, ctl, reqdesc;
 };
 
 ts_status alloc_units(PlainWork &w, PipeBufs &b, uint64_t units, cudaStream_t s)
@@ -1038,7 +1168,9 @@ ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_par
     TS_CHECK(read_dev_status(st));
     c.tiles = (uint64_t)hdr[HDR_T_LO] | ((uint64_t)hdr[HDR_T_HI] << 32);
     TS_CHECK(w.tiles.alloc(sizeof(uint32_t) * (c.tiles ? c.tiles : 1), s));
+    TS_CHECK(w.tdesc.alloc(sizeof(uint4) * (c.tiles ? c.tiles : 1), s));
     TS_CHECK(w.tile_off.alloc(sizeof(uint64_t) * (c.tiles + 1), s));
+    b.tdesc = w.tdesc.as<uint4>();
     b.tile_hits = w.tiles.as<uint32_t>();
     b.tile_off = w.tile_off.as<uint64_t>();
 

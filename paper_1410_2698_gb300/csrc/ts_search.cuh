@@ -19,6 +19,9 @@ namespace ts {
 constexpr int PK_WARPS = 8;
 constexpr int PK_THREADS = PK_WARPS * 32;
 constexpr int PK_CH = 64;      // records per bulk-copy stage (2 KB): 2 per lane
+constexpr int PK_QUEUE = 64;   // exact-test queue per warp (drained at 32)
+constexpr uint32_t PK_MAX_TILES = (1u << 29) - 1;  // tile index bits of a queued candidate
+constexpr int PK_SPARSE = 8;  // chunks met by at most this many members: per-member sweep
 constexpr int PK_TILE = 256;   // records per tile (multiple of PK_CH)
 constexpr int GROUP = 32;      // units per group
 constexpr int PK_MIN_BLOCKS = 2;  // resident pair-kernel blocks per SM the register budget targets
@@ -55,6 +58,8 @@ struct PipeBufs {
     uint32_t *ntiles;
     uint64_t *tile_base;  // groups + 1
     // tiles and rows
+    uint4 *tdesc;         // per tile: {first member (sorted unit slot), s0, s1,
+                          //            sel | (members - 1) << 3 | request << 8}
     uint32_t *tile_hits;
     uint64_t *tile_off;   // tiles + 1
     uint32_t *out_q, *out_e;
@@ -104,7 +109,12 @@ ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
 ts_status pipe_scan_rows(const PipeBufs &b, const PipeCaps &c, cudaStream_t s);
 ts_status pipe_write(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,
                      cudaStream_t s);
-int key_bits(const Index *ix, uint32_t nreq);
+// Layout of a unit's sort key: request | array (sel_bits) | top lo_bits bits of the range start.
+struct KeyFmt {
+    int lo_bits = 0, lo_shift = 0, sel_bits = 0;
+};
+constexpr int KEY_LO_BITS = 13;
+KeyFmt key_fmt(const Index *ix);
 ts_status search_brute_noalloc(const ts_segments *db, const ts_segments *q,
                                const ts_query_params *qp, uint32_t *q_idx, uint32_t *e_idx,
                                double *t_in, double *t_out, uint64_t capacity, uint64_t *count,
