@@ -44,6 +44,11 @@ def parse():
     ap.add_argument("--indexes", default="spatiotemporal,temporal,spatial")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-index", default="spatiotemporal")
+    ap.add_argument("--served-requests", type=int, default=200)
+    ap.add_argument("--served-max-traj", type=int, default=500)
+    ap.add_argument("--served-rho", type=float, default=0.9)
     return ap.parse_args()
 
 
@@ -353,6 +358,10 @@ def run_gpu(args):
     }
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, api, w, plans, kinds)
+    if not args.no_served and rank == 0:
+        sk = args.served_index
+        sidx = indexes[sk] if sk in indexes else api.ts_build_index(w.db, kind=sk)
+        line["served"] = run_served(args, api, w, sidx)
     if world > 1:
         dist.barrier()
     if rank == 0 and not args.no_cpu:
@@ -395,6 +404,96 @@ def run_e2e(args, api, w, plans, kinds):
     t = sum(ms) / 1e3
     return {"value": qsegs * len(ms) / t, "unit": "query segs/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h}
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def run_served(args, api, w, index):
+    """The served form on the resident database: a stream of requests (each a set of query
+    trajectory runs with its own interval and d, query arrays on the host) through the request
+    loop, against one plain ts_search per request. Three passes over the same requests:
+    plain (one after another, each synchronous), served at saturation (all submitted at once) and
+    served with Poisson arrivals at rho x the plain request rate. Latency = completion - arrival
+    (the server's clock); every result is released after its count is read."""
+    import threading
+    from paper_1410_2698_gb300 import workloads
+    stream = workloads.served_stream(w, n_requests=args.served_requests, rate_per_s=1.0,
+                                     max_traj=args.served_max_traj)
+    qsegs = sum(r.queries.n for r in stream)
+    max_q = max(r.queries.n for r in stream)
+    # plain: one synchronous search per request (after two warm-up searches)
+    for r in stream[:2]:
+        api.ts_search(index, r.queries, r.d, r.t_start, r.t_end).free()
+    lat_plain, rows_plain = [], 0
+    t0 = time.perf_counter()
+    for r in stream:
+        a = time.perf_counter()
+        res = api.ts_search(index, r.queries, r.d, r.t_start, r.t_end)
+        rows_plain += res.count
+        res.free()
+        lat_plain.append((time.perf_counter() - a) * 1e3)
+    plain_s = time.perf_counter() - t0
+    mu_plain = len(stream) / plain_s
+    srv = api.Server(index, max_batch_requests=64, max_batch_queries=max(1 << 20, 2 * max_q),
+                     max_batch_rows=1 << 25, max_inflight=2, use_graph=True, linger_us=200)
+    try:
+        def serve(arrivals):
+            tickets = [None] * len(stream)
+            start = time.perf_counter()
+
+            def submitter():
+                for i, r in enumerate(stream):
+                    if arrivals is not None:
+                        dt = start + arrivals[i] - time.perf_counter()
+                        if dt > 0:
+                            time.sleep(dt)
+                    tickets[i] = srv.submit(r.queries, r.d, r.t_start, r.t_end)
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            lat, rows, sizes = [], 0, []
+            for i in range(len(stream)):
+                while tickets[i] is None:
+                    time.sleep(1e-5)
+                res, tm = srv.wait(tickets[i], timeout_ms=600000)
+                rows += res.count
+                res.free()
+                lat.append((tm["done_us"] - tm["submit_us"]) / 1e3)
+                sizes.append(tm["batch_requests"])
+            th.join()
+            return time.perf_counter() - start, lat, rows, sizes
+
+        serve(None)  # warm-up: plans captured as graphs
+        sat_s, lat_sat, rows_sat, sizes_sat = serve(None)
+        lam = args.served_rho * mu_plain
+        arrivals = [r.arrival_s / lam for r in stream]  # the stream's gaps are at rate 1
+        poi_s, lat_poi, rows_poi, sizes_poi = serve(arrivals)
+    finally:
+        srv.close()
+    if not (rows_plain == rows_sat == rows_poi):
+        raise RuntimeError("served and plain forms disagree on the result count")
+    return {
+        "index": index_kind_name(index),
+        "requests": len(stream), "query_segs": qsegs, "rows": rows_plain,
+        "workload": f"{len(stream)} requests of 1-{args.served_max_traj} query trajectory runs "
+                    f"(log-uniform) of 10-200 segments, interval = the runs' span, d log-uniform "
+                    f"in [0.5, 10]; query arrays on the host",
+        "plain": {"qsegs_per_s": qsegs / plain_s, "req_per_s": mu_plain,
+                  "p50_ms": _pct(lat_plain, 50), "p99_ms": _pct(lat_plain, 99)},
+        "saturated": {"qsegs_per_s": qsegs / sat_s, "req_per_s": len(stream) / sat_s,
+                      "p50_ms": _pct(lat_sat, 50), "p99_ms": _pct(lat_sat, 99),
+                      "mean_batch_requests": float(np.mean(sizes_sat))},
+        "poisson": {"rho": args.served_rho, "arrival_rate_req_s": lam,
+                    "qsegs_per_s": qsegs / poi_s, "p50_ms": _pct(lat_poi, 50),
+                    "p99_ms": _pct(lat_poi, 99), "mean_batch_requests": float(np.mean(sizes_poi))},
+    }
+
+
+def index_kind_name(index):
+    return {0: "brute", 1: "spatial", 2: "temporal", 3: "spatiotemporal"}.get(
+        int(index.info()["kind"]), "?")
 
 
 def cpu_baseline(w, budget_s=8.0):

@@ -287,12 +287,11 @@ static ts_status enqueue_run(BatchPlan *p, cudaStream_t s, bool write)
     TS_LAUNCHED();
     const double *cols[8];
     for (int c = 0; c < 8; c++) cols[c] = p->d_cat + (uint64_t)c * k.nq;
-    // sort keys of unused unit slots must be the largest key
-    TS_CUDA(cudaMemsetAsync(b.keys, 0xff, sizeof(uint64_t) * k.units, s));
-    if (grid) TS_CUDA(cudaMemsetAsync(b.qnu, 0, sizeof(uint32_t) * k.nq, s));
+    // every stage below sizes its work from the run's counts in device memory (the header and
+    // the run header), not from the plan's capacities
     TS_CHECK(pipe_prepare(p->ix, cols, k.nq, p->d_reqs, k.nreq, b, k, s));
     if (grid) {
-        TS_CHECK(scan_u32(b.qnu, b.quoff, k.nq, b.status, s));
+        TS_CHECK(scan_u32(b.qnu, b.quoff, k.nq, b.status, s, p->d_run));
         TS_CHECK(pipe_grid_units(p->ix, k.nq, b, k, s));
     }
     TS_CHECK(pipe_group(p->ix, k.nreq, b, k, s));

@@ -122,6 +122,23 @@ __host__ __device__ inline int part_of(double x, double lo, double w, int v)
     return j;
 }
 
+// The same part with the first guess taken from a precomputed reciprocal inv_w ~ 1 / w (a
+// multiplication instead of a division); the exact boundary comparisons correct the guess, so
+// the result equals part_of's.
+__host__ __device__ inline int part_of_r(double x, double lo, double w, double inv_w, int v)
+{
+    if (!(x >= lo)) return -1;
+    if (v <= 1 || !(w > 0.0)) return v - 1;
+    double f = floor((x - lo) * inv_w);
+    int j;
+    if (!(f < (double)v)) j = v - 1;
+    else if (f < 0.0) j = 0;
+    else j = (int)f;
+    while (j + 1 < v && part_bound(lo, w, j + 1) <= x) j++;
+    while (j > 0 && part_bound(lo, w, j) > x) j--;
+    return j;
+}
+
 // ---------------------------------------------------------------------------------------------
 // host-side error plumbing
 // ---------------------------------------------------------------------------------------------
@@ -175,15 +192,20 @@ struct DevBuf {
 // ---------------------------------------------------------------------------------------------
 // primitives (ts_prims.cu)
 // ---------------------------------------------------------------------------------------------
+// The primitives take a capacity n and optionally n_dev, a device word holding the actual count
+// (<= n) of a run whose size only the device knows; the work then follows the actual count.
 // exclusive scan of n u32 values into n+1 u64 offsets (out[n] = total)
-ts_status scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s);
+ts_status scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s,
+                          const uint32_t *n_dev = nullptr);
 // exclusive scan of n u32 values into n+1 u32 offsets; sets DEV_ERR_OVERFLOW in *status when the
 // total does not fit in 32 bits
 ts_status scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *status,
-                   cudaStream_t s);
+                   cudaStream_t s, const uint32_t *n_dev = nullptr);
 // stable LSD radix sort of (key, value) pairs by the low `bits` bits of the key
-ts_status radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s);
-ts_status radix_sort_u32(uint32_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s);
+ts_status radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s,
+                         const uint32_t *n_dev = nullptr);
+ts_status radix_sort_u32(uint32_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s,
+                         const uint32_t *n_dev = nullptr);
 
 }  // namespace ts
 

@@ -8,6 +8,8 @@
 
 #include <atomic>
 
+#include <algorithm>
+
 #include "ts_internal.cuh"
 
 namespace ts {
@@ -105,10 +107,22 @@ __device__ inline T block_excl_scan(T v, T *total)
     return excl;
 }
 
-template <class Tin, class Tout>
-__global__ void k_tile_sums(const Tin *in, uint64_t n, Tout *sums)
+// Element count of a primitive: the capacity, or the smaller count held in device memory (a
+// run whose size is known only on the device, e.g. a replayed CUDA graph).
+__device__ __forceinline__ uint64_t dev_count(uint64_t cap, const uint32_t *n_dev)
 {
-    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    return n_dev ? min(cap, (uint64_t)*n_dev) : cap;
+}
+
+template <class Tin, class Tout>
+__global__ void k_tile_sums(const Tin *in, uint64_t ncap, const uint32_t *n_dev, Tout *sums)
+{
+    const uint64_t n = dev_count(ncap, n_dev);
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    if (base >= n) {
+        if (threadIdx.x == 0) sums[blockIdx.x] = 0;
+        return;
+    }
     Tout acc = 0;
     for (int k = 0; k < SCAN_ITEMS; k++) {
         uint64_t i = base + (uint64_t)k * SCAN_THREADS + threadIdx.x;
@@ -120,12 +134,14 @@ __global__ void k_tile_sums(const Tin *in, uint64_t n, Tout *sums)
 }
 
 // Scan one tile per block with the tile's starting offset taken from `tile_off` (or 0), writing
-// out[i] = exclusive prefix; the last block also writes out[n] = total when tile_off holds the
-// grand total at index gridDim.x.
+// out[i] = exclusive prefix; the block whose tile holds index n writes out[n] = total.
 template <class Tin, class Tout>
-__global__ void k_tile_scan(const Tin *in, uint64_t n, const Tout *tile_off, Tout *out)
+__global__ void k_tile_scan(const Tin *in, uint64_t ncap, const uint32_t *n_dev,
+                            const Tout *tile_off, Tout *out)
 {
-    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    const uint64_t n = dev_count(ncap, n_dev);
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    if (base > n) return;
     Tout v[SCAN_ITEMS];
     Tout acc = 0;
     // thread-contiguous items for a stable sequential order within a thread
@@ -145,41 +161,90 @@ __global__ void k_tile_scan(const Tin *in, uint64_t n, const Tout *tile_off, Tou
         if (i < n) out[i] = off;
         off += v[k];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+    if (threadIdx.x == 0 && n < base + SCAN_TILE)
         out[n] = (tile_off ? tile_off[blockIdx.x] : Tout(0)) + total;
 }
 
+// Second pass of a two-kernel scan: every block first adds up the totals of the tiles before its
+// own (at most SCAN_LOOKBACK of them, read by the whole block), then scans its tile.
+constexpr uint64_t SCAN_LOOKBACK = 4096;
+
 template <class Tin, class Tout>
-static ts_status scan_impl(const Tin *in, Tout *out, uint64_t n, cudaStream_t s)
+__global__ void k_tile_scan_lb(const Tin *in, uint64_t ncap, const uint32_t *n_dev,
+                               const Tout *sums, Tout *out)
+{
+    const uint64_t n = dev_count(ncap, n_dev);
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    if (base > n) return;
+    Tout pre = 0;
+    for (uint32_t j = threadIdx.x; j < blockIdx.x; j += SCAN_THREADS) pre += sums[j];
+    Tout before;
+    block_excl_scan<Tout>(pre, &before);
+    Tout v[SCAN_ITEMS];
+    Tout acc = 0;
+    const uint64_t tbase = base + (uint64_t)threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        const uint64_t i = tbase + k;
+        v[k] = i < n ? (Tout)in[i] : Tout(0);
+        acc += v[k];
+    }
+    Tout total;
+    Tout off = before + block_excl_scan<Tout>(acc, &total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        const uint64_t i = tbase + k;
+        if (i < n) out[i] = off;
+        off += v[k];
+    }
+    if (threadIdx.x == 0 && n < base + SCAN_TILE) out[n] = before + total;
+}
+
+// Exclusive scan of n (or *n_dev <= n) values: out[0..n] with out[n] = total. One block per tile
+// of SCAN_TILE values plus one, so that the tile holding index n always exists.
+template <class Tin, class Tout>
+static ts_status scan_impl(const Tin *in, Tout *out, uint64_t n, const uint32_t *n_dev,
+                           cudaStream_t s)
 {
     if (n == 0) {
         TS_CUDA(cudaMemsetAsync(out, 0, sizeof(Tout), s));
         return TS_OK;
     }
-    uint64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+    const uint64_t nt = n / SCAN_TILE + 1;
     if (nt == 1) {
-        k_tile_scan<Tin, Tout><<<1, SCAN_THREADS, 0, s>>>(in, n, nullptr, out);
+        k_tile_scan<Tin, Tout><<<1, SCAN_THREADS, 0, s>>>(in, n, n_dev, nullptr, out);
         TS_LAUNCHED();
         return TS_OK;
     }
-    DevBuf sums, offs;
+    DevBuf sums;
     TS_CHECK(sums.alloc(sizeof(Tout) * nt, s));
-    TS_CHECK(offs.alloc(sizeof(Tout) * (nt + 1), s));
-    k_tile_sums<Tin, Tout><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, sums.as<Tout>());
+    k_tile_sums<Tin, Tout><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, n_dev, sums.as<Tout>());
     TS_LAUNCHED();
-    TS_CHECK((scan_impl<Tout, Tout>(sums.as<Tout>(), offs.as<Tout>(), nt, s)));
-    k_tile_scan<Tin, Tout><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, offs.as<Tout>(), out);
+    if (nt <= SCAN_LOOKBACK) {
+        k_tile_scan_lb<Tin, Tout><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, n_dev,
+                                                                        sums.as<Tout>(), out);
+        TS_LAUNCHED();
+        return TS_OK;
+    }
+    DevBuf offs;
+    TS_CHECK(offs.alloc(sizeof(Tout) * (nt + 1), s));
+    TS_CHECK((scan_impl<Tout, Tout>(sums.as<Tout>(), offs.as<Tout>(), nt, nullptr, s)));
+    k_tile_scan<Tin, Tout><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, n_dev, offs.as<Tout>(),
+                                                                 out);
     TS_LAUNCHED();
     return TS_OK;
 }
 
-ts_status scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s)
+ts_status scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s,
+                          const uint32_t *n_dev)
 {
-    return scan_impl<uint32_t, uint64_t>(in, out, n, s);
+    return scan_impl<uint32_t, uint64_t>(in, out, n, n_dev, s);
 }
 
-__global__ void k_narrow_u64(const uint64_t *in, uint32_t *out, uint64_t n, uint32_t *status)
+__global__ void k_narrow_u64(const uint64_t *in, uint32_t *out, uint64_t ncap,
+                             const uint32_t *n_dev, uint32_t *status)
 {
+    const uint64_t n = dev_count(ncap, n_dev);
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i > n) return;
     uint64_t v = in[i];
@@ -191,13 +256,13 @@ __global__ void k_narrow_u64(const uint64_t *in, uint32_t *out, uint64_t n, uint
 }
 
 ts_status scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *status,
-                   cudaStream_t s)
+                   cudaStream_t s, const uint32_t *n_dev)
 {
     DevBuf wide;
     TS_CHECK(wide.alloc(sizeof(uint64_t) * (n + 1), s));
-    TS_CHECK(scan_u32_to_u64(in, wide.as<uint64_t>(), n, s));
+    TS_CHECK(scan_u32_to_u64(in, wide.as<uint64_t>(), n, s, n_dev));
     k_narrow_u64<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(wide.as<uint64_t>(), out, n,
-                                                                   status);
+                                                                   n_dev, status);
     TS_LAUNCHED();
     return TS_OK;
 }
@@ -215,9 +280,11 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
 constexpr int RS_RADIX = 256;
 
 template <class K>
-__global__ void k_rs_hist(const K *keys, uint64_t n, int shift, uint32_t *hist, uint32_t ntiles)
+__global__ void k_rs_hist(const K *keys, uint64_t ncap, const uint32_t *n_dev, int shift,
+                          uint32_t *hist, uint32_t ntiles)
 {
     __shared__ uint32_t h[RS_RADIX];
+    const uint64_t n = dev_count(ncap, n_dev);
     for (int i = threadIdx.x; i < RS_RADIX; i += RS_THREADS) h[i] = 0;
     __syncthreads();
     uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
@@ -233,11 +300,13 @@ __global__ void k_rs_hist(const K *keys, uint64_t n, int shift, uint32_t *hist, 
 template <class K>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K *keys_in, const uint32_t *vals_in,
                                                            K *keys_out, uint32_t *vals_out,
-                                                           uint64_t n, int shift,
-                                                           const uint64_t *digit_off,
+                                                           uint64_t ncap, const uint32_t *n_dev,
+                                                           int shift, const uint64_t *digit_off,
                                                            uint32_t ntiles)
 {
     __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
+    const uint64_t n = dev_count(ncap, n_dev);
+    if ((uint64_t)blockIdx.x * RS_TILE >= n) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * RS_RADIX; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
     __syncthreads();
@@ -288,7 +357,20 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K *keys_in, con
 }
 
 template <class K>
-static ts_status radix_sort_impl(K *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s)
+__global__ void k_copy_kv(const K *ks, const uint32_t *vs, K *kd, uint32_t *vd, uint64_t ncap,
+                          const uint32_t *n_dev)
+{
+    const uint64_t n = dev_count(ncap, n_dev);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        kd[i] = ks[i];
+        vd[i] = vs[i];
+    }
+}
+
+template <class K>
+static ts_status radix_sort_impl(K *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s,
+                                 const uint32_t *n_dev)
 {
     if (n <= 1 || bits <= 0) return TS_OK;
     uint32_t ntiles = (uint32_t)((n + RS_TILE - 1) / RS_TILE);
@@ -303,30 +385,39 @@ static ts_status radix_sort_impl(K *keys, uint32_t *vals, uint64_t n, int bits, 
     int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_rs_hist<K><<<ntiles, RS_THREADS, 0, s>>>(ka, n, shift, hist.as<uint32_t>(), ntiles);
+        k_rs_hist<K><<<ntiles, RS_THREADS, 0, s>>>(ka, n, n_dev, shift, hist.as<uint32_t>(),
+                                                   ntiles);
         TS_LAUNCHED();
         TS_CHECK(scan_u32_to_u64(hist.as<uint32_t>(), off.as<uint64_t>(), nh, s));
-        k_rs_scatter<K><<<ntiles, RS_THREADS, 0, s>>>(ka, va, kbp, vbp, n, shift,
+        k_rs_scatter<K><<<ntiles, RS_THREADS, 0, s>>>(ka, va, kbp, vbp, n, n_dev, shift,
                                                       off.as<uint64_t>(), ntiles);
         TS_LAUNCHED();
         K *tk = ka; ka = kbp; kbp = tk;
         uint32_t *tv = va; va = vbp; vbp = tv;
     }
     if (ka != keys) {
-        TS_CUDA(cudaMemcpyAsync(keys, ka, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
-        TS_CUDA(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+        if (n_dev) {
+            const unsigned cb = (unsigned)std::min<uint64_t>((n + 255) / 256, 152 * 8);
+            k_copy_kv<K><<<cb, 256, 0, s>>>(ka, va, keys, vals, n, n_dev);
+            TS_LAUNCHED();
+        } else {
+            TS_CUDA(cudaMemcpyAsync(keys, ka, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
+            TS_CUDA(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+        }
     }
     return TS_OK;
 }
 
-ts_status radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s)
+ts_status radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s,
+                         const uint32_t *n_dev)
 {
-    return radix_sort_impl<uint64_t>(keys, vals, n, bits, s);
+    return radix_sort_impl<uint64_t>(keys, vals, n, bits, s, n_dev);
 }
 
-ts_status radix_sort_u32(uint32_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s)
+ts_status radix_sort_u32(uint32_t *keys, uint32_t *vals, uint64_t n, int bits, cudaStream_t s,
+                         const uint32_t *n_dev)
 {
-    return radix_sort_impl<uint32_t>(keys, vals, n, bits, s);
+    return radix_sort_impl<uint32_t>(keys, vals, n, bits, s, n_dev);
 }
 
 }  // namespace ts

@@ -97,10 +97,10 @@ struct PrepParams {
     const double *bin_start, *bin_pmax;
     const uint32_t *bin_off;
     uint32_t v[3];
-    double sub_lo[3], sub_w[3];
+    double sub_lo[3], sub_w[3], sub_iw[3];  // iw: reciprocal of the width
     const uint32_t *st_off[3];
     uint32_t g;
-    double g_lo[3], g_w[3], longest[3];
+    double g_lo[3], g_w[3], g_iw[3], longest[3];
     PipeBufs b;
 };
 
@@ -118,6 +118,8 @@ __global__ void k_qprep(PrepParams P)
 {
     const uint64_t nq = P.b.run ? min((uint64_t)P.b.run[0], P.nq) : P.nq;
     const uint32_t nreq = P.b.run ? P.b.run[1] : P.nreq;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && P.kind != TS_INDEX_SPATIAL)
+        P.b.hdr[HDR_NU] = (uint32_t)nq;  // one unit slot per query
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t r = req_of(P.reqs, nreq, (uint32_t)i);
@@ -168,8 +170,8 @@ __global__ void k_qprep(PrepParams P)
                 double a = ((mn[d] - R.d) - P.longest[d]) -
                            EXT_SLACK * ((fabs(mn[d]) + R.d) + P.longest[d]);
                 double bb = (mx[d] + R.d) + EXT_SLACK * (fabs(mx[d]) + R.d);
-                int pa = part_of(a, P.g_lo[d], P.g_w[d], (int)P.g);
-                int pb = part_of(bb, P.g_lo[d], P.g_w[d], (int)P.g);
+                int pa = part_of_r(a, P.g_lo[d], P.g_w[d], P.g_iw[d], (int)P.g);
+                int pb = part_of_r(bb, P.g_lo[d], P.g_w[d], P.g_iw[d], (int)P.g);
                 if (pa < 0) pa = 0;
                 if (pb < pa) any = false;
                 ca[d] = (uint32_t)pa;
@@ -200,8 +202,9 @@ __global__ void k_qprep(PrepParams P)
                             const int vv = (int)P.v[d];
                             double a = (mn[d] - R.d) - EXT_SLACK * (fabs(mn[d]) + R.d);
                             double bb = (mx[d] + R.d) + EXT_SLACK * (fabs(mx[d]) + R.d);
-                            const int pa = part_of(a, P.sub_lo[d], P.sub_w[d], vv);
-                            const int pb = part_of(bb, P.sub_lo[d], P.sub_w[d], vv);
+                            const double iw = P.sub_iw[d];
+                            const int pa = part_of_r(a, P.sub_lo[d], P.sub_w[d], iw, vv);
+                            const int pb = part_of_r(bb, P.sub_lo[d], P.sub_w[d], iw, vv);
                             const int ja = pa < 0 ? 0 : pa, jb = pb;
                             uint32_t clo, chi;
                             if (jb < ja) {
@@ -251,6 +254,8 @@ __global__ void k_grid_units(uint64_t nqcap, uint64_t ucap, KeyFmt kf, uint32_t 
                              const uint32_t *g_off, PipeBufs b)
 {
     const uint64_t nq = b.run ? min((uint64_t)b.run[0], nqcap) : nqcap;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        b.hdr[HDR_NU] = (uint32_t)min((uint64_t)b.quoff[nq], ucap);  // unit slots of the runs
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t nu = b.qnu[i];
@@ -305,74 +310,102 @@ __global__ void k_req_scan(uint32_t nreq_cap, PipeBufs b)
     b.hdr[HDR_G] = gs;
 }
 
+// One warp per group: lane p holds the group's member p; the members are ordered by (array,
+// start) with a bitonic network over the lanes, and their ranges are merged into disjoint
+// segments (a member opens a segment when its start lies beyond every earlier range of its
+// array); each segment is cut into tiles of `tile` records.
 __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, PipeBufs b)
 {
+    const unsigned FULL = 0xffffffffu;
     const uint32_t nreq = b.run ? min(b.run[1], nreq_cap) : nreq_cap;
     const uint32_t G = b.hdr[HDR_G];
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < gcap;
-         g += (uint64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < gcap;
+         g += warps) {
         if (g >= G) {
-            b.ntiles[g] = 0;
+            if (lane == 0) b.ntiles[g] = 0;
             continue;
         }
         uint32_t lo = 0, hi = nreq;  // last r with gstart[r] <= g
         while (hi - lo > 1) {
-            uint32_t mid = (lo + hi) / 2;
+            const uint32_t mid = (lo + hi) / 2;
             if (b.gstart[mid] <= g) lo = mid; else hi = mid;
         }
         const uint32_t r = lo;
         const uint32_t first = b.ustart[r] + GROUP * ((uint32_t)g - b.gstart[r]);
         const uint32_t end = min(first + GROUP, b.ustart[r] + b.req_units[r]);
-        b.g_first[g] = first;
-        b.g_count[g] = end - first;
-        // order the members by (array, start), then merge their ranges into disjoint segments
-        uint32_t ms[GROUP], ml[GROUP], mh[GROUP];
         const uint32_t n = end - first;
-        for (uint32_t p = 0; p < n; p++) {
-            const uint32_t u = b.vals[first + p];
-            uint32_t s = b.u_sel[u], l = b.u_lo[u], h = b.u_hi[u];
-            uint32_t j = p;
-            for (; j > 0 && (ms[j - 1] > s || (ms[j - 1] == s && ml[j - 1] > l)); j--) {
-                ms[j] = ms[j - 1];
-                ml[j] = ml[j - 1];
-                mh[j] = mh[j - 1];
-            }
-            ms[j] = s;
-            ml[j] = l;
-            mh[j] = h;
+        if (lane == 0) {
+            b.g_first[g] = first;
+            b.g_count[g] = n;
         }
-        uint32_t nseg = 0, tiles = 0;
-        uint32_t cs = 0, clo = 0, chi = 0;
-        bool open = false;
-        uint32_t *slo = b.seg_lo + (uint64_t)g * GROUP, *shi = b.seg_hi + (uint64_t)g * GROUP;
-        uint32_t *ssel = b.seg_sel + (uint64_t)g * GROUP, *st0 = b.seg_t0 + (uint64_t)g * GROUP;
-        for (uint32_t p = 0; p < n; p++) {
-            const uint32_t s = ms[p], ul = ml[p], uh = mh[p];
-            if (open && s == cs && ul <= chi) {
-                chi = max(chi, uh);
-                continue;
-            }
-            if (open) {
-                slo[nseg] = clo; shi[nseg] = chi; ssel[nseg] = cs; st0[nseg] = tiles;
-                tiles += (chi - clo + tile - 1) / tile;
-                nseg++;
-            }
-            open = true;
-            cs = s; clo = ul; chi = uh;
+        // key = (array, start); lanes past the group's members hold the largest key
+        uint64_t key = ~0ull;
+        uint32_t mh = 0;
+        if ((uint32_t)lane < n) {
+            const uint32_t u = b.vals[first + lane];
+            key = ((uint64_t)b.u_sel[u] << 32) | b.u_lo[u];
+            mh = b.u_hi[u];
         }
-        if (open) {
-            slo[nseg] = clo; shi[nseg] = chi; ssel[nseg] = cs; st0[nseg] = tiles;
-            tiles += (chi - clo + tile - 1) / tile;
-            nseg++;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const uint64_t ok = __shfl_xor_sync(FULL, key, j);
+                const uint32_t oh = __shfl_xor_sync(FULL, mh, j);
+                const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+                if (keep_min ? (ok < key) : (ok > key)) {
+                    key = ok;
+                    mh = oh;
+                }
+            }
         }
-        b.g_nseg[g] = nseg;
-        b.ntiles[g] = tiles;
+        const bool member = (uint32_t)lane < n;
+        const uint32_t sel = (uint32_t)(key >> 32), ml = (uint32_t)key;
+        // running maximum of the range ends over the earlier members of the same array
+        uint32_t run = mh;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(FULL, run, o);
+            const uint32_t vs = __shfl_up_sync(FULL, sel, o);
+            if (lane >= o && vs == sel) run = max(run, v);
+        }
+        const uint32_t prev_run = __shfl_up_sync(FULL, run, 1);
+        const uint32_t prev_sel = __shfl_up_sync(FULL, sel, 1);
+        const bool start = member && (lane == 0 || prev_sel != sel || ml > prev_run);
+        const unsigned starts = __ballot_sync(FULL, start);
+        const unsigned nmask = n >= 32 ? FULL : ((1u << n) - 1u);
+        const unsigned ends = n ? (((starts >> 1) | (1u << (n - 1))) & nmask) : 0u;
+        // segment k ends at the lane before the next start (or at the last member)
+        const bool is_end = n > 0 && ((ends >> lane) & 1u);
+        const uint32_t a = 31 - __clz(starts & (lane == 31 ? FULL : ((2u << lane) - 1u)));
+        const uint32_t seg_lo = __shfl_sync(FULL, ml, a & 31);
+        const uint32_t ntile = is_end ? (run - seg_lo + tile - 1) / tile : 0u;
+        uint32_t incl = ntile;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (is_end) {
+            const uint32_t k = __popc(starts & (lane == 31 ? FULL : ((2u << lane) - 1u))) - 1;
+            const uint64_t o = (uint64_t)g * GROUP + k;
+            b.seg_lo[o] = seg_lo;
+            b.seg_hi[o] = run;
+            b.seg_sel[o] = sel;
+            b.seg_t0[o] = incl - ntile;
+        }
+        if (lane == 31) {
+            b.g_nseg[g] = __popc(starts);
+            b.ntiles[g] = incl;
+        }
     }
 }
 
 __global__ void k_hdr(uint64_t gcap, uint64_t tcap, PipeBufs b)
 {
-    const uint64_t T = b.tile_base[gcap];
+    const uint64_t T = b.tile_base[min((uint64_t)b.hdr[HDR_G], gcap)];
     b.hdr[HDR_T_LO] = (uint32_t)T;
     b.hdr[HDR_T_HI] = (uint32_t)(T >> 32);
     b.stats[ST_GROUPS] = b.hdr[HDR_G];
@@ -406,6 +439,7 @@ __global__ void k_tile_desc(uint64_t gcap, uint64_t tcap, uint32_t tile, PipeBuf
                 const uint32_t s1 = min(hi, s0 + tile);
                 b.tdesc[base + t0 + j] =
                     make_uint4(first, s0, s1, sel | ((count - 1) << 3) | (r << 8));
+                b.tile_hits[base + t0 + j] = 0;  // the count pass adds to it
             }
         }
     }
@@ -878,9 +912,11 @@ ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq
         P.v[d] = ix->v[d];
         P.sub_lo[d] = ix->sub_lo[d];
         P.sub_w[d] = ix->sub_w[d];
+        P.sub_iw[d] = ix->sub_w[d] > 0.0 ? 1.0 / ix->sub_w[d] : 0.0;
         P.st_off[d] = ix->st_off[d];
         P.g_lo[d] = ix->g_lo[d];
         P.g_w[d] = ix->g_w[d];
+        P.g_iw[d] = ix->g_w[d] > 0.0 ? 1.0 / ix->g_w[d] : 0.0;
         P.longest[d] = ix->longest[d];
     }
     P.g = ix->g;
@@ -909,12 +945,13 @@ ts_status pipe_group(const Index *ix, uint32_t nreq, const PipeBufs &b, const Pi
     // one bit above the key fields: a unit without candidates has key ~0 and sorts last
     const KeyFmt f = key_fmt(ix);
     const int bits = f.lo_bits + f.sel_bits + bits_for(nreq > 1 ? nreq - 1 : 0) + 1;
-    TS_CHECK(radix_sort_u64(b.keys, b.vals, c.units, bits, s));
+    TS_CHECK(radix_sort_u64(b.keys, b.vals, c.units, bits, s, b.hdr + HDR_NU));
     k_req_scan<<<1, 32, 0, s>>>(nreq, b);
     TS_LAUNCHED();
-    k_groups<<<nblk(c.groups), TPB, 0, s>>>(nreq, c.groups, c.tile, b);
+    const unsigned gblk = (unsigned)std::min<uint64_t>((c.groups * 32 + TPB - 1) / TPB, 152 * 16);
+    k_groups<<<gblk, TPB, 0, s>>>(nreq, c.groups, c.tile, b);
     TS_LAUNCHED();
-    TS_CHECK(scan_u32_to_u64(b.ntiles, b.tile_base, c.groups, s));
+    TS_CHECK(scan_u32_to_u64(b.ntiles, b.tile_base, c.groups, s, b.hdr + HDR_G));
     k_hdr<<<1, 1, 0, s>>>(c.groups, c.tiles, b);
     TS_LAUNCHED();
     return TS_OK;
@@ -929,7 +966,6 @@ ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
     PairParams P;
     fill_pair_params(P, ix, reqs, b, c);
     if (c.tiles) {
-        TS_CUDA(cudaMemsetAsync(b.tile_hits, 0, sizeof(uint32_t) * c.tiles, s));
         const unsigned dblk = (unsigned)std::min<uint64_t>((c.groups * 32 + TPB - 1) / TPB, 152 * 16);
         k_tile_desc<<<dblk, TPB, 0, s>>>(c.groups, c.tiles, c.tile, b);
         TS_LAUNCHED();
@@ -941,7 +977,7 @@ ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
 
 ts_status pipe_scan_rows(const PipeBufs &b, const PipeCaps &c, cudaStream_t s)
 {
-    return scan_u32_to_u64(b.tile_hits, b.tile_off, c.tiles, s);
+    return scan_u32_to_u64(b.tile_hits, b.tile_off, c.tiles, s, b.hdr + HDR_T_LO);
 }
 
 ts_status pipe_write(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,

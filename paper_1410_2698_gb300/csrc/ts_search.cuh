@@ -26,7 +26,8 @@ constexpr int PK_TILE = 256;   // records per tile (multiple of PK_CH)
 constexpr int GROUP = 32;      // units per group
 constexpr int PK_MIN_BLOCKS = 2;  // resident pair-kernel blocks per SM the register budget targets
 
-enum { HDR_U = 0, HDR_G = 1, HDR_T_LO = 2, HDR_T_HI = 3, HDR_N = 4 };
+// run header words: valid units, groups, tiles (low, high), unit slots holding a sort key
+enum { HDR_U = 0, HDR_G = 1, HDR_T_LO = 2, HDR_T_HI = 3, HDR_NU = 4, HDR_N = 5 };
 
 // One request of a batch (device memory).
 struct ReqDesc {
