@@ -205,13 +205,16 @@ ts_status ts_search_batch(const ts_index *idx, uint32_t nreq, const ts_segments 
  * use_graph, is captured once in a CUDA graph and replayed. */
 typedef struct ts_batch_params {
     uint32_t max_requests;  /* requests per run, < 2^24 */
-    uint32_t tile_records;  /* candidate records per work tile, multiple of 64 (0 = 256) */
+    uint32_t tile_records;  /* candidate records per work tile, multiple of 64, <= 2048 (0 = 256) */
     uint64_t max_queries;   /* query segments per run, all requests together */
     uint64_t max_rows;      /* result rows per run, all requests together */
     uint64_t max_units;     /* candidate ranges per run (0 = derived) */
     uint64_t max_tiles;     /* work tiles per run (0 = derived) */
     int32_t use_graph;      /* 1: capture the run in a CUDA graph once, then replay it */
     int32_t pair_blocks;    /* blocks of the persistent pair kernel (0 = all resident) */
+    uint64_t scratch_rows;  /* hits the count pass keeps (32 B each) and places after the scan;
+                               a run with more hits sweeps its tiles a second time to write them
+                               (0 = min(max_rows, 2^24)) */
 } ts_batch_params;
 
 typedef struct ts_batch ts_batch;

@@ -78,7 +78,8 @@ class ts_batch_params(ctypes.Structure):
     _fields_ = [("max_requests", ctypes.c_uint32), ("tile_records", ctypes.c_uint32),
                 ("max_queries", ctypes.c_uint64), ("max_rows", ctypes.c_uint64),
                 ("max_units", ctypes.c_uint64), ("max_tiles", ctypes.c_uint64),
-                ("use_graph", ctypes.c_int32), ("pair_blocks", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("pair_blocks", ctypes.c_int32),
+                ("scratch_rows", ctypes.c_uint64)]
 
 
 class ts_batch_status(ctypes.Structure):

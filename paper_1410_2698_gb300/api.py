@@ -315,11 +315,12 @@ class BatchPlan:
     CUDA graph."""
 
     def __init__(self, index: Index, max_requests, max_queries, max_rows, tile_records=0,
-                 use_graph=True, pair_blocks=0, max_units=0, max_tiles=0, stream=None):
+                 use_graph=True, pair_blocks=0, max_units=0, max_tiles=0, stream=None,
+                 scratch_rows=0):
         lib = _lib.load()
         p = _lib.ts_batch_params(int(max_requests), int(tile_records), int(max_queries),
                                  int(max_rows), int(max_units), int(max_tiles), int(use_graph),
-                                 int(pair_blocks))
+                                 int(pair_blocks), int(scratch_rows))
         h = ctypes.c_void_p()
         check(lib.ts_batch_create(index.handle, ctypes.byref(p), _current_stream(stream),
                                   ctypes.byref(h)))

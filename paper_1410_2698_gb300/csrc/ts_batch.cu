@@ -110,6 +110,12 @@ static void layout(BatchPlan *p, Carver &c)
     b.ntiles = c.take<uint32_t>(k.groups);
     b.tile_base = c.take<uint64_t>(k.groups + 1);
     b.tdesc = c.take<uint4>(k.tiles);
+    b.s_tile = c.take<uint32_t>(k.scratch);
+    b.s_rank = c.take<uint32_t>(k.scratch);
+    b.s_q = c.take<uint32_t>(k.scratch);
+    b.s_e = c.take<uint32_t>(k.scratch);
+    b.s_tin = c.take<double>(k.scratch);
+    b.s_tout = c.take<double>(k.scratch);
     b.tile_hits = c.take<uint32_t>(k.tiles);
     b.tile_off = c.take<uint64_t>(k.tiles + 1);
     if (p->own_rows) {
@@ -155,8 +161,9 @@ ts_status create_plan(const Index *ix, const ts_batch_params *prm, cudaStream_t 
         return TS_ERR_INVALID_ARG;
     }
     const uint32_t tile = prm->tile_records ? prm->tile_records : (uint32_t)PK_TILE;
-    if (tile % PK_CH != 0 || tile > (1u << 26)) {
-        set_error("batch plan: tile_records must be a multiple of %d", PK_CH);
+    if (tile % PK_CH != 0 || tile > 32 * PK_CH) {
+        set_error("batch plan: tile_records must be a multiple of %d, at most %d", PK_CH,
+                  32 * PK_CH);
         return TS_ERR_INVALID_ARG;
     }
     std::unique_ptr<BatchPlan, void (*)(BatchPlan *)> p(new BatchPlan(), destroy_plan);
@@ -173,6 +180,12 @@ ts_status create_plan(const Index *ix, const ts_batch_params *prm, cudaStream_t 
     k.groups = k.units / GROUP + k.nreq + 1;
     k.tiles = prm->max_tiles ? prm->max_tiles : 64 * k.groups + 65536;
     k.rows = own_rows ? prm->max_rows : ~0ull;
+    // hits the count pass keeps for placement after the scan; more hits than this make the
+    // write pass sweep the tiles again
+    k.scratch = prm->scratch_rows
+                    ? prm->scratch_rows
+                    : std::min<uint64_t>(own_rows ? prm->max_rows : 4 * k.nq + (1ull << 20),
+                                         SCRATCH_MAX);
     Carver sz;
     layout(p.get(), sz);
     p->dbytes = sz.off;

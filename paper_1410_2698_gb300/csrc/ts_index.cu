@@ -135,6 +135,58 @@ __global__ void k_gather(SegIn in, uint64_t n, const uint32_t *perm, SegD *seg, 
     orig[s] = i;
 }
 
+// Key of an entry inside its bin: (bin, x of its FP32 box centre as an order-preserving integer).
+// Any order inside a bin leaves every bin's range unchanged; x order makes aligned chunks of 64
+// entries narrow in x, so a chunk's bounding record rejects most queries.
+__global__ void k_tx_key(const RecF *rec, const uint32_t *bin_of, uint64_t n, uint64_t *keys,
+                         uint32_t *vals)
+{
+    const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const RecF r = rec[s];
+    uint32_t u = __float_as_uint(0.5f * r.xmin + 0.5f * r.xmax + 0.0f);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    keys[s] = ((uint64_t)bin_of[s] << 32) | u;
+    vals[s] = (uint32_t)s;
+}
+
+// Bounding record of every aligned chunk of 64 records, a warp per chunk.
+__global__ void k_chunk_box(const RecF *rec, uint64_t n, uint64_t nchunks, RecF *box)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t c = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks;
+         c += warps) {
+        float lo[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+        float hi[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int h = 0; h < 2; h++) {
+            const uint64_t i = c * 64 + h * 32 + lane;
+            if (i < n) {
+                const RecF r = rec[i];
+                lo[0] = fminf(lo[0], r.xmin); hi[0] = fmaxf(hi[0], r.xmax);
+                lo[1] = fminf(lo[1], r.ymin); hi[1] = fmaxf(hi[1], r.ymax);
+                lo[2] = fminf(lo[2], r.zmin); hi[2] = fmaxf(hi[2], r.zmax);
+                lo[3] = fminf(lo[3], r.t0); hi[3] = fmaxf(hi[3], r.t1);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+                hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+            }
+        if (lane == 0) {
+            RecF b;
+            b.xmin = lo[0]; b.xmax = hi[0];
+            b.ymin = lo[1]; b.ymax = hi[1];
+            b.zmin = lo[2]; b.zmax = hi[2];
+            b.t0 = lo[3]; b.t1 = hi[3];
+            box[c] = b;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // temporal bins
 // ---------------------------------------------------------------------------------------------
@@ -525,6 +577,29 @@ ts_status build_index(const ts_segments *db, const ts_index_params *p, cudaStrea
     TS_LAUNCHED();
     k_prefix_max<<<1, 1024, 0, s>>>(ix->bin_end, ix->m, ix->bin_pmax);
     TS_LAUNCHED();
+
+    if (p->kind != TS_INDEX_SPATIAL) {
+        // bins ordered by x inside (ranges over the start-time order cover whole bins)
+        DevBuf tkeys, tvals;
+        TS_CHECK(tkeys.alloc(sizeof(uint64_t) * n, s));
+        TS_CHECK(tvals.alloc(sizeof(uint32_t) * n, s));
+        k_tx_key<<<nblocks(n), TPB, 0, s>>>(ix->rec, bin_of.as<uint32_t>(), n,
+                                            tkeys.as<uint64_t>(), tvals.as<uint32_t>());
+        TS_LAUNCHED();
+        TS_CHECK(radix_sort_u64(tkeys.as<uint64_t>(), tvals.as<uint32_t>(), n,
+                                32 + bits_for((uint64_t)ix->m - 1), s));
+        const uint64_t nchunks = (n + 63) / 64;
+        TS_CHECK(ix->alloc(&ix->trec, n));
+        TS_CHECK(ix->alloc(&ix->tid, n));
+        TS_CHECK(ix->alloc(&ix->tbox, nchunks));
+        TS_CUDA(cudaMemcpyAsync(ix->tid, tvals.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice,
+                                s));
+        k_gather_rec<<<nblocks(n), TPB, 0, s>>>(ix->tid, n, ix->rec, ix->trec);
+        TS_LAUNCHED();
+        const unsigned cb = (unsigned)std::min<uint64_t>((nchunks * 32 + TPB - 1) / TPB, 152 * 32);
+        k_chunk_box<<<cb, TPB, 0, s>>>(ix->trec, n, nchunks, ix->tbox);
+        TS_LAUNCHED();
+    }
 
     if (p->kind == TS_INDEX_SPATIOTEMPORAL || p->kind == TS_INDEX_SPATIAL) {
         DevBuf lo3, hi3;

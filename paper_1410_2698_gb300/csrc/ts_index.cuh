@@ -25,6 +25,13 @@ struct Index {
     double tmin = 0, tmax = 0, max_dur = 0;
     double emin[3] = {0, 0, 0}, emax[3] = {0, 0, 0}, longest[3] = {0, 0, 0};
 
+    // the entries of every temporal bin once more, ordered by x inside the bin (the bins keep
+    // their ranges [B^first, B^last]): records, their start-time positions, and the bounding
+    // record of every aligned chunk of 64 (built for every kind whose ranges cover bins)
+    RecF *trec = nullptr;
+    uint32_t *tid = nullptr;
+    RecF *tbox = nullptr;
+
     // temporal bins (Sec. 4.2)
     uint32_t m = 0;
     double b = 0;

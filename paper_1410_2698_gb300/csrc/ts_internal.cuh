@@ -66,7 +66,7 @@ enum : uint32_t {
 // Stats slots (u64 array in device memory).
 enum : int {
     ST_QSEGS = 0, ST_TESTS = 1, ST_EXACT = 2, ST_HITS = 3, ST_TILES = 4, ST_GROUPS = 5,
-    ST_SUBBIN = 6, ST_NSLOTS = 8
+    ST_SUBBIN = 6, ST_SCRATCH = 7, ST_NSLOTS = 8  // ST_SCRATCH: hits offered to the scratch
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -166,6 +166,10 @@ void note_launch();
     } while (0)
 
 // Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
+// Stream-ordered allocation from the library's pool (freed blocks stay pooled); inside a stream
+// capture a graph memory node. Release with cudaFreeAsync.
+cudaError_t pool_malloc(void **p, size_t nbytes, cudaStream_t stream);
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;

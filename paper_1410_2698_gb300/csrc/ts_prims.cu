@@ -9,6 +9,7 @@
 #include <atomic>
 
 #include <algorithm>
+#include <mutex>
 
 #include "ts_internal.cuh"
 
@@ -52,13 +53,49 @@ void DevBuf::release()
     bytes = 0;
 }
 
+// The library's stream-ordered pool of a device: freed blocks stay in the pool (no release
+// threshold), so the work buffers of repeated searches are not mapped and unmapped every call.
+static cudaMemPool_t work_pool()
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
+cudaError_t pool_malloc(void **p, size_t nbytes, cudaStream_t stream)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(stream, &cs);
+    cudaMemPool_t pool = cs == cudaStreamCaptureStatusNone ? work_pool() : nullptr;
+    return pool ? cudaMallocFromPoolAsync(p, nbytes, pool, stream)
+                : cudaMallocAsync(p, nbytes, stream);
+}
+
 ts_status DevBuf::alloc(size_t nbytes, cudaStream_t stream)
 {
     release();
     s = stream;
     bytes = nbytes;
     if (nbytes == 0) nbytes = 256;
-    cudaError_t e = cudaMallocAsync(&p, nbytes, stream);
+    cudaError_t e = pool_malloc(&p, nbytes, stream);
     if (e != cudaSuccess) {
         p = nullptr;
         return cuda_status(e, "cudaMallocAsync");

@@ -314,7 +314,8 @@ __global__ void k_req_scan(uint32_t nreq_cap, PipeBufs b)
 // start) with a bitonic network over the lanes, and their ranges are merged into disjoint
 // segments (a member opens a segment when its start lies beyond every earlier range of its
 // array); each segment is cut into tiles of `tile` records.
-__global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, PipeBufs b)
+__global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, uint32_t align_sels,
+                         PipeBufs b)
 {
     const unsigned FULL = 0xffffffffu;
     const uint32_t nreq = b.run ? min(b.run[1], nreq_cap) : nreq_cap;
@@ -345,7 +346,10 @@ __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, PipeBu
         uint32_t mh = 0;
         if ((uint32_t)lane < n) {
             const uint32_t u = b.vals[first + lane];
-            key = ((uint64_t)b.u_sel[u] << 32) | b.u_lo[u];
+            const uint32_t us = b.u_sel[u];
+            uint32_t ul = b.u_lo[u];
+            if ((align_sels >> us) & 1u) ul &= ~(uint32_t)(PK_CH - 1);  // chunk-aligned tiles
+            key = ((uint64_t)us << 32) | ul;
             mh = b.u_hi[u];
         }
 #pragma unroll
@@ -466,12 +470,28 @@ struct PairParams {
     const ReqDesc *reqs;
     const RecF *rec[5];
     const uint32_t *ids[5];
+    const RecF *box[5];  // bounding record per aligned chunk of 64 records, or null
     const SegD *seg;
     const uint32_t *orig;
     uint64_t tcap;
     uint64_t rows_cap;  // write pass: rows beyond this capacity are not written (flagged)
+    uint64_t scap;      // hits the count pass keeps for placement (0: none)
     uint32_t tile;      // records per tile
 };
+
+// Exact FP64 test of one (query, entry) pair and, when `interval`, its hit interval. Not inlined:
+// the pair kernel calls it only for the candidates that passed both FP32 filters, so the registers
+// it needs are saved around the call instead of being reserved across the whole sweep.
+__device__ __noinline__ bool exact_test(const QueryD *qp, const SegD *ep, bool interval,
+                                        double *tin, double *tout)
+{
+    const SegD e = *ep;
+    const QueryD q = *qp;
+    Quad qd;
+    if (!(pair_quad(q, e, q.pad, qd) && quad_hit(qd))) return false;
+    if (interval) quad_interval(qd, tin, tout);
+    return true;
+}
 
 // Persistent pair kernel. Warps take tiles (a group of up to 32 query units and up to `tile`
 // consecutive entries of one sorted array) from a device counter. Entry records stream through
@@ -503,6 +523,8 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
 
     uint64_t ntiles = (uint64_t)B.hdr[HDR_T_LO] | ((uint64_t)B.hdr[HDR_T_HI] << 32);
     if (ntiles > P.tcap || ntiles > PK_MAX_TILES) ntiles = 0;  // overflow already flagged
+    if (PASS == PASS_WRITE && P.scap && B.stats[ST_SCRATCH] <= P.scap)
+        ntiles = 0;  // the count pass kept every hit: k_place writes the rows
     if (PASS == PASS_WRITE && ntiles && B.tile_off[ntiles] > P.rows_cap) {
         // more rows than the output holds: write none (the caller sees the exact count)
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, DEV_ERR_OVERFLOW);
@@ -510,7 +532,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
     }
     unsigned long long acc_tests = 0, acc_exact = 0, acc_hits = 0;
     uint32_t qn = 0;                            // queued candidates (warp-uniform)
-    uint32_t wt_cur = 0xffffffffu, wt_cnt = 0;  // write pass: last tile with rows, rows so far
+    uint32_t wt_cur = 0xffffffffu, wt_cnt = 0;  // last tile with hits, its hits so far
 
     // Exact test of the oldest nflush queued candidates, one per lane.
     auto flush = [&](uint32_t nflush) {
@@ -519,7 +541,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             qi = W.q_qi[lane];
             pos = W.q_pos[lane];
             tw = W.q_tile[lane];
-            if (PASS == PASS_WRITE) ql = W.q_ql[lane];
+            ql = W.q_ql[lane];
         }
         __syncwarp();
         if (qn > nflush && (uint32_t)lane < qn - nflush) {
@@ -527,7 +549,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             W.q_qi[lane] = W.q_qi[j];
             W.q_pos[lane] = W.q_pos[j];
             W.q_tile[lane] = W.q_tile[j];
-            if (PASS == PASS_WRITE) W.q_ql[lane] = W.q_ql[j];
+            W.q_ql[lane] = W.q_ql[j];
         }
         __syncwarp();
         qn -= nflush;
@@ -539,13 +561,8 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         if ((uint32_t)lane < nflush) {
             const uint32_t *ids = P.ids[tw >> 29];
             eid = ids ? ids[pos] : pos;
-            const SegD e = P.seg[eid];
-            const QueryD q = B.qd[qi];
-            Quad qd;
-            if (pair_quad(q, e, q.pad, qd) && quad_hit(qd)) {
-                h = true;
-                if (PASS == PASS_WRITE) quad_interval(qd, &tin, &tout);
-            }
+            h = exact_test(B.qd + qi, P.seg + eid, PASS == PASS_WRITE || P.scap != 0, &tin,
+                           &tout);
         }
         const unsigned hm = __ballot_sync(FULL, h);
         if (!hm) return;
@@ -553,27 +570,40 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         // hits of the same tile (the queue holds a tile's candidates contiguously, tiles in the
         // order this warp took them)
         const unsigned mine = hm & __match_any_sync(FULL, h ? tile : 0xffffffffu);
+        // rank of the hit among its tile's rows (queue order, the same in both passes)
+        const uint32_t rank = (tile == wt_cur ? wt_cnt : 0u) + __popc(mine & lt_mask);
         if (PASS == PASS_COUNT) {
             if (h && (mine & lt_mask) == 0) atomicAdd(&B.tile_hits[tile], (uint32_t)__popc(mine));
-        } else {
-            if (h) {
-                const uint64_t o = B.tile_off[tile] + (tile == wt_cur ? wt_cnt : 0u) +
-                                   __popc(mine & lt_mask);
-                if (o < B.tile_off[tile + 1]) {
-                    B.out_q[o] = ql;
-                    B.out_e[o] = P.orig[eid];
-                    B.out_tin[o] = tin;
-                    B.out_tout[o] = tout;
-                } else {
-                    atomicOr(B.status, DEV_ERR_INTERNAL);  // the passes disagree
+            if (P.scap) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&B.stats[ST_SCRATCH], (unsigned long long)__popc(hm));
+                base = __shfl_sync(FULL, base, 0);
+                const unsigned long long slot = base + __popc(hm & lt_mask);
+                if (h && slot < P.scap) {
+                    B.s_tile[slot] = tile;
+                    B.s_rank[slot] = rank;
+                    B.s_q[slot] = ql;
+                    B.s_e[slot] = P.orig[eid];
+                    B.s_tin[slot] = tin;
+                    B.s_tout[slot] = tout;
                 }
             }
-            const int last = 31 - __clz(hm);
-            const uint32_t last_tile = __shfl_sync(FULL, tile, last);
-            const uint32_t last_n = __popc(__shfl_sync(FULL, mine, last));
-            wt_cnt = (last_tile == wt_cur ? wt_cnt : 0u) + last_n;
-            wt_cur = last_tile;
+        } else if (h) {
+            const uint64_t o = B.tile_off[tile] + rank;
+            if (o < B.tile_off[tile + 1]) {
+                B.out_q[o] = ql;
+                B.out_e[o] = P.orig[eid];
+                B.out_tin[o] = tin;
+                B.out_tout[o] = tout;
+            } else {
+                atomicOr(B.status, DEV_ERR_INTERNAL);  // the passes disagree
+            }
         }
+        const int last = 31 - __clz(hm);
+        const uint32_t last_tile = __shfl_sync(FULL, tile, last);
+        const uint32_t last_n = __popc(__shfl_sync(FULL, mine, last));
+        wt_cnt = (last_tile == wt_cur ? wt_cnt : 0u) + last_n;
+        wt_cur = last_tile;
     };
 
     // tiles are taken from a device counter; the next index is fetched while a tile is swept
@@ -646,7 +676,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                     W.q_qi[j] = qi;
                     W.q_pos[j] = pos;
                     W.q_tile[j] = tw;
-                    if (PASS == PASS_WRITE) W.q_ql[j] = qi - q_first;
+                    W.q_ql[j] = qi - q_first;
                 }
                 qn += __popc(bm);
                 if (qn >= 32) {
@@ -656,8 +686,25 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             }
         };
 
-        for (uint32_t c = 0; c < nch && !abort; c++) {
-            const int st = c & 1;
+        // the chunks this lane's member meets: its range overlaps the chunk and, for an array
+        // with chunk boxes, its expanded box meets the chunk's bounding record
+        const RecF *bx = P.box[sel];
+        uint32_t mc = 0u;
+        for (uint32_t c = 0; c < nch; c++) {
+            const uint32_t cs = s0 + c * PK_CH, ce = min(cs + (uint32_t)PK_CH, s1);
+            bool meet = lo < ce && hi > cs;
+            if (bx && meet) meet = filter_box(bx[cs / PK_CH], ea, eb);
+            mc |= (uint32_t)meet << c;
+        }
+        // chunks to sweep, in order; the first two were copied already, later ones are copied
+        // two sweeps ahead, so a chunk no member meets is neither copied nor swept
+        const uint32_t need = __reduce_or_sync(FULL, mc);
+        uint32_t todo = need | (nch > 1 ? 3u : 1u);
+        uint32_t pend = todo & ~3u;
+        for (uint32_t k = 0; todo && !abort; k++) {
+            const uint32_t c = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int st = k & 1;
             if (!mbar_wait_bounded(&W.bar[st], parity[st])) {
                 abort = true;
                 break;
@@ -666,10 +713,11 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             pending[st] = false;
             const uint32_t cs = s0 + c * PK_CH;
             const uint32_t cn = min((uint32_t)PK_CH, s1 - cs);
+            const bool mine = (mc >> c) & 1u;
             // this lane's own range within the chunk, as bits of the 64 stage slots
             const uint32_t va = max(lo, cs), vb = min(hi, cs + cn);
             uint32_t v0 = 0u, v1 = 0u;
-            if (vb > va) {
+            if (mine && vb > va) {
                 const uint32_t x = va - cs, y = vb - cs;  // 0 <= x < y <= 64
                 v0 = (y >= 32 ? FULL : ((1u << y) - 1u)) & (x >= 32 ? 0u : (FULL << x));
                 v1 = y <= 32 ? 0u : ((y >= 64 ? FULL : ((1u << (y - 32)) - 1u)) &
@@ -677,7 +725,9 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             }
             uint32_t m0 = 0u, m1 = 0u;
             const unsigned act = __ballot_sync(FULL, (v0 | v1) != 0u);
-            if (__popc(act) <= PK_SPARSE) {
+            if (!act) {
+                // (a chunk copied ahead of the member tests that no member meets)
+            } else if (__popc(act) <= PK_SPARSE) {
                 // few members meet this chunk: one lane per slot (slots lane and lane + 32), the
                 // members that meet the chunk in turn, their boxes read as broadcasts
                 const bool in0 = (uint32_t)lane < cn, in1 = (uint32_t)lane + 32 < cn;
@@ -735,9 +785,11 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 enqueue(p, myq, cs + i);
             }
             __syncwarp();
-            if (c + 2 < nch) {
+            if (pend) {
+                const uint32_t cnext = __ffs(pend) - 1;
+                pend &= pend - 1u;
                 if (lane == 0) {
-                    const uint32_t ns = s0 + (c + 2) * PK_CH, nn = min((uint32_t)PK_CH, s1 - ns);
+                    const uint32_t ns = s0 + cnext * PK_CH, nn = min((uint32_t)PK_CH, s1 - ns);
                     mbar_arrive_tx(&W.bar[st], nn * (uint32_t)sizeof(RecF));
                     bulk_g2s(&W.stage[st][0], recs + ns, nn * (uint32_t)sizeof(RecF), &W.bar[st]);
                 }
@@ -764,6 +816,34 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             atomicAdd(&B.stats[ST_EXACT], acc_exact);
             atomicAdd(&B.stats[ST_HITS], acc_hits);
         }
+    }
+}
+
+// Rows of the hits the count pass kept: row = the tile's scanned offset + the hit's rank in the
+// tile, the same row the write pass's sweep would give it. Does nothing when the scratch
+// overflowed (the write pass sweeps instead) or the rows exceed the output capacity.
+__global__ void k_place(PipeBufs b, uint64_t scap, uint64_t tcap, uint64_t rows_cap)
+{
+    const unsigned long long n = b.stats[ST_SCRATCH];
+    if (n > scap) return;
+    const uint64_t T = (uint64_t)b.hdr[HDR_T_LO] | ((uint64_t)b.hdr[HDR_T_HI] << 32);
+    if (T > tcap || T > PK_MAX_TILES) return;  // overflow already flagged
+    if (b.tile_off[T] > rows_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(b.status, DEV_ERR_OVERFLOW);
+        return;
+    }
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = b.s_tile[i];
+        const uint64_t o = b.tile_off[t] + b.s_rank[i];
+        if (t >= T || o >= b.tile_off[t + 1]) {
+            atomicOr(b.status, DEV_ERR_INTERNAL);
+            continue;
+        }
+        b.out_q[o] = b.s_q[i];
+        b.out_e[o] = b.s_e[i];
+        b.out_tin[o] = b.s_tin[i];
+        b.out_tout[o] = b.s_tout[i];
     }
 }
 
@@ -797,14 +877,19 @@ void fill_pair_params(PairParams &P, const Index *ix, const ReqDesc *reqs, const
         P.rec[k] = ix->st_rec[k];
         P.ids[k] = ix->st_ids[k];
     }
-    P.rec[SEL_T] = ix->rec;
-    P.ids[SEL_T] = nullptr;
+    // ranges over the start-time order cover whole bins: they are swept in the copy ordered by
+    // x inside every bin, chunk by chunk with the chunks' bounding records
+    P.rec[SEL_T] = ix->trec ? ix->trec : ix->rec;
+    P.ids[SEL_T] = ix->trec ? ix->tid : nullptr;
+    for (int k = 0; k < 5; k++) P.box[k] = nullptr;
+    P.box[SEL_T] = ix->tbox;
     P.rec[SEL_GRID] = ix->ga_rec;
     P.ids[SEL_GRID] = ix->ga;
     P.seg = ix->seg;
     P.orig = ix->orig;
     P.tcap = c.tiles;
     P.rows_cap = c.rows;
+    P.scap = c.scratch;
     P.tile = c.tile;
 }
 
@@ -949,7 +1034,7 @@ ts_status pipe_group(const Index *ix, uint32_t nreq, const PipeBufs &b, const Pi
     k_req_scan<<<1, 32, 0, s>>>(nreq, b);
     TS_LAUNCHED();
     const unsigned gblk = (unsigned)std::min<uint64_t>((c.groups * 32 + TPB - 1) / TPB, 152 * 16);
-    k_groups<<<gblk, TPB, 0, s>>>(nreq, c.groups, c.tile, b);
+    k_groups<<<gblk, TPB, 0, s>>>(nreq, c.groups, c.tile, ix->tbox ? (1u << SEL_T) : 0u, b);
     TS_LAUNCHED();
     TS_CHECK(scan_u32_to_u64(b.ntiles, b.tile_base, c.groups, s, b.hdr + HDR_G));
     k_hdr<<<1, 1, 0, s>>>(c.groups, c.tiles, b);
@@ -989,6 +1074,10 @@ ts_status pipe_write(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
     PairParams P;
     fill_pair_params(P, ix, reqs, b, c);
     if (c.tiles) {
+        if (c.scratch) {
+            k_place<<<152 * 4, TPB, 0, s>>>(b, c.scratch, c.tiles, c.rows);
+            TS_LAUNCHED();
+        }
         k_pair<PASS_WRITE><<<blocks, PK_THREADS, sizeof(WarpSmem) * PK_WARPS, s>>>(P);
         TS_LAUNCHED();
     }
@@ -1062,7 +1151,7 @@ namespace {
 // Work buffers of a plain search, allocated stage by stage at their exact sizes.
 struct PlainWork {
     DevBuf qd, qf, qreq, qcell, qnu, quoff, u_q, u_lo, u_hi, u_sel, keys, vals, req, groups, segs,
-        ntiles, tile_base, tiles, tdesc, tile_off, ctl, reqdesc;
+        ntiles, tile_base, tiles, tdesc, tile_off, ctl, reqdesc, scratch;
 };
 
 ts_status alloc_units(PlainWork &w, PipeBufs &b, uint64_t units, cudaStream_t s)
@@ -1208,6 +1297,15 @@ ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_par
     TS_CHECK(w.tile_off.alloc(sizeof(uint64_t) * (c.tiles + 1), s));
     b.tdesc = w.tdesc.as<uint4>();
     b.tile_hits = w.tiles.as<uint32_t>();
+    // hits kept by the count pass and placed after the scan (a second sweep when they overflow)
+    c.scratch = std::min<uint64_t>(4 * nq + (1ull << 20), SCRATCH_MAX);
+    TS_CHECK(w.scratch.alloc(32 * c.scratch, s));
+    b.s_tile = w.scratch.as<uint32_t>();
+    b.s_rank = b.s_tile + c.scratch;
+    b.s_q = b.s_rank + c.scratch;
+    b.s_e = b.s_q + c.scratch;
+    b.s_tin = reinterpret_cast<double *>(b.s_e + c.scratch);
+    b.s_tout = b.s_tin + c.scratch;
     b.tile_off = w.tile_off.as<uint64_t>();
 
     EventPair ev_count, ev_write;
@@ -1235,10 +1333,10 @@ ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_par
         return TS_ERR_CAPACITY;
     }
     if (total == 0) return TS_OK;
-    TS_CUDA(cudaMallocAsync((void **)&out->q, sizeof(uint32_t) * total, s));
-    TS_CUDA(cudaMallocAsync((void **)&out->e, sizeof(uint32_t) * total, s));
-    TS_CUDA(cudaMallocAsync((void **)&out->tin, sizeof(double) * total, s));
-    TS_CUDA(cudaMallocAsync((void **)&out->tout, sizeof(double) * total, s));
+    TS_CUDA(pool_malloc((void **)&out->q, sizeof(uint32_t) * total, s));
+    TS_CUDA(pool_malloc((void **)&out->e, sizeof(uint32_t) * total, s));
+    TS_CUDA(pool_malloc((void **)&out->tin, sizeof(double) * total, s));
+    TS_CUDA(pool_malloc((void **)&out->tout, sizeof(double) * total, s));
     b.out_q = out->q;
     b.out_e = out->e;
     b.out_tin = out->tin;

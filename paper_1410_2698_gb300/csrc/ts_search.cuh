@@ -24,7 +24,7 @@ constexpr uint32_t PK_MAX_TILES = (1u << 29) - 1;  // tile index bits of a queue
 constexpr int PK_SPARSE = 8;  // chunks met by at most this many members: per-member sweep
 constexpr int PK_TILE = 256;   // records per tile (multiple of PK_CH)
 constexpr int GROUP = 32;      // units per group
-constexpr int PK_MIN_BLOCKS = 2;  // resident pair-kernel blocks per SM the register budget targets
+constexpr int PK_MIN_BLOCKS = 3;  // resident pair-kernel blocks per SM the register budget targets
 
 // run header words: valid units, groups, tiles (low, high), unit slots holding a sort key
 enum { HDR_U = 0, HDR_G = 1, HDR_T_LO = 2, HDR_T_HI = 3, HDR_NU = 4, HDR_N = 5 };
@@ -65,6 +65,9 @@ struct PipeBufs {
     uint64_t *tile_off;   // tiles + 1
     uint32_t *out_q, *out_e;
     double *out_tin, *out_tout;
+    // hits found by the count pass (tile, rank in the tile, row), placed after the scan
+    uint32_t *s_tile, *s_rank, *s_q, *s_e;
+    double *s_tin, *s_tout;
     // control
     uint32_t *hdr;
     unsigned long long *stats;
@@ -78,7 +81,9 @@ struct PipeCaps {
     uint32_t nreq = 1;
     uint32_t tile = PK_TILE;  // records per tile (multiple of PK_CH)
     int pair_blocks = 0;      // pair kernel grid (0 = all resident blocks)
+    uint64_t scratch = 0;     // hits the count pass keeps for placement (0: the write pass sweeps)
 };
+constexpr uint64_t SCRATCH_MAX = 1ull << 24;  // rows (32 B each)
 
 // Result of one search (device arrays owned by the ts_result handle).
 struct SearchOut {

@@ -101,10 +101,10 @@ ts_status take_rows(BatchPlan *p, uint32_t r, SrvReq *q)
     q->out.stats.n_hits = count;
     if (!count) return TS_OK;
     cudaStream_t st = p->stream;
-    TS_CUDA(cudaMallocAsync((void **)&q->out.q, 4 * count, st));
-    TS_CUDA(cudaMallocAsync((void **)&q->out.e, 4 * count, st));
-    TS_CUDA(cudaMallocAsync((void **)&q->out.tin, 8 * count, st));
-    TS_CUDA(cudaMallocAsync((void **)&q->out.tout, 8 * count, st));
+    TS_CUDA(pool_malloc((void **)&q->out.q, 4 * count, st));
+    TS_CUDA(pool_malloc((void **)&q->out.e, 4 * count, st));
+    TS_CUDA(pool_malloc((void **)&q->out.tin, 8 * count, st));
+    TS_CUDA(pool_malloc((void **)&q->out.tout, 8 * count, st));
     TS_CUDA(cudaMemcpyAsync(q->out.q, p->b.out_q + first, 4 * count, cudaMemcpyDeviceToDevice, st));
     TS_CUDA(cudaMemcpyAsync(q->out.e, p->b.out_e + first, 4 * count, cudaMemcpyDeviceToDevice, st));
     TS_CUDA(cudaMemcpyAsync(q->out.tin, p->b.out_tin + first, 8 * count, cudaMemcpyDeviceToDevice, st));

@@ -87,6 +87,31 @@ def test_plan_runs_equal_plain(use_graph):
     plan.free()
 
 
+@pytest.mark.parametrize("kind", ["temporal", "spatial"])
+def test_plan_rows_equal_with_and_without_scratch(kind):
+    """The count pass keeps its hits for placement after the scan; with a scratch too small for
+    them the write pass sweeps the tiles again. Both give the same rows in the same order."""
+    w = workloads.tiny()
+    idx = api.ts_build_index(w.db, kind=kind)
+    reqs = [(w.queries, d, 0.0, 70.0) for d in (1.0, 5.0)]
+    out = []
+    for scratch in (0, 8):
+        plan = api.BatchPlan(idx, max_requests=2, max_queries=4000, max_rows=400000,
+                             max_units=1 << 20, use_graph=True, scratch_rows=scratch)
+        plan.run(reqs)
+        st = plan.wait()
+        assert not st["overflow"]
+        assert st["rows"] > 8
+        out.append([plan.request_to_host(r) for r in range(len(reqs))])
+        plan.free()
+    for a, b in zip(*out):
+        _same(a, b)  # unsorted: the same row order
+    for r, req in enumerate(reqs):
+        b = out[0][r]
+        order = np.lexsort((b["e_idx"], b["q_idx"]))
+        _same({k: v[order] for k, v in b.items()}, _plain(idx, req))
+
+
 def test_plan_reports_overflow_with_exact_count():
     w = workloads.tiny()
     idx = api.ts_build_index(w.db, kind="temporal")
