@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="records per work tile (0 = default)")
+    ap.add_argument("--pair-blocks", type=int, default=0, help="pair kernel blocks (0 = all)")
     ap.add_argument("--served-index", default="spatiotemporal")
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-max-traj", type=int, default=500)
@@ -238,7 +240,7 @@ def run_gpu(args):
     plans = {k: api.BatchPlan(indexes[k], max_requests=len(reqs),
                               max_queries=w.queries.n * len(reqs),
                               max_rows=max(1 << 20, 2 * rows_per_batch[k]), use_graph=True,
-                              stream=0)
+                              stream=0, tile_records=args.tile, pair_blocks=args.pair_blocks)
              for k in kinds}
     batch_stats = []
 
@@ -342,7 +344,8 @@ def run_gpu(args):
                                f"d in {list(w.distances)}, indexes {kinds}",
                    "form": "batched: per index one reusable plan replayed as a CUDA graph, the "
                            "distances are the requests of one batch",
-                   "l2": "flushed (256 MB write) before every timed step"},
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "tile_records": args.tile or 256, "pair_blocks": args.pair_blocks or "all"},
         "tests_per_s": btot["n_tests"] * world / (batch_total / 1e3),
         "hits_per_step": btot["n_hits"] // max(args.steps, 1),
         "gpu_launches": int(l2 - l1),

@@ -103,6 +103,7 @@ static void layout(BatchPlan *p, Carver &c)
     b.g_first = c.take<uint32_t>(k.groups);
     b.g_count = c.take<uint32_t>(k.groups);
     b.g_nseg = c.take<uint32_t>(k.groups);
+    b.gmem = c.take<MemberRec>(GROUP * k.groups);
     b.seg_lo = c.take<uint32_t>(GROUP * k.groups);
     b.seg_hi = c.take<uint32_t>(GROUP * k.groups);
     b.seg_sel = c.take<uint32_t>(GROUP * k.groups);

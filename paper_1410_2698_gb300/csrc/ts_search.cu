@@ -317,6 +317,7 @@ __global__ void k_req_scan(uint32_t nreq_cap, PipeBufs b)
 __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, uint32_t align_sels,
                          PipeBufs b)
 {
+    // (also writes the members' records, in the group's order, for the pair kernel)
     const unsigned FULL = 0xffffffffu;
     const uint32_t nreq = b.run ? min(b.run[1], nreq_cap) : nreq_cap;
     const uint32_t G = b.hdr[HDR_G];
@@ -343,9 +344,10 @@ __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, uint32
         }
         // key = (array, start); lanes past the group's members hold the largest key
         uint64_t key = ~0ull;
-        uint32_t mh = 0;
+        uint32_t mh = 0, mu = 0;
         if ((uint32_t)lane < n) {
             const uint32_t u = b.vals[first + lane];
+            mu = u;
             const uint32_t us = b.u_sel[u];
             uint32_t ul = b.u_lo[u];
             if ((align_sels >> us) & 1u) ul &= ~(uint32_t)(PK_CH - 1);  // chunk-aligned tiles
@@ -358,15 +360,27 @@ __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, uint32
             for (int j = k >> 1; j > 0; j >>= 1) {
                 const uint64_t ok = __shfl_xor_sync(FULL, key, j);
                 const uint32_t oh = __shfl_xor_sync(FULL, mh, j);
+                const uint32_t ou = __shfl_xor_sync(FULL, mu, j);
                 const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
                 if (keep_min ? (ok < key) : (ok > key)) {
                     key = ok;
                     mh = oh;
+                    mu = ou;
                 }
             }
         }
         const bool member = (uint32_t)lane < n;
         const uint32_t sel = (uint32_t)(key >> 32), ml = (uint32_t)key;
+        if (member) {
+            MemberRec mr;
+            mr.qi = b.u_q[mu];
+            mr.lo = b.u_lo[mu];
+            mr.hi = b.u_hi[mu];
+            mr.sel = sel;
+            mr.ea = b.qf[2 * (uint64_t)mr.qi + 0];
+            mr.eb = b.qf[2 * (uint64_t)mr.qi + 1];
+            b.gmem[(uint64_t)g * GROUP + lane] = mr;
+        }
         // running maximum of the range ends over the earlier members of the same array
         uint32_t run = mh;
 #pragma unroll
@@ -442,7 +456,7 @@ __global__ void k_tile_desc(uint64_t gcap, uint64_t tcap, uint32_t tile, PipeBuf
                 const uint32_t s0 = lo + j * tile;
                 const uint32_t s1 = min(hi, s0 + tile);
                 b.tdesc[base + t0 + j] =
-                    make_uint4(first, s0, s1, sel | ((count - 1) << 3) | (r << 8));
+                    make_uint4((uint32_t)g, s0, s1, sel | ((count - 1) << 3) | (r << 8));
                 b.tile_hits[base + t0 + j] = 0;  // the count pass adds to it
             }
         }
@@ -454,13 +468,13 @@ __global__ void k_tile_desc(uint64_t gcap, uint64_t tcap, uint32_t tile, PipeBuf
 // ---------------------------------------------------------------------------------------------
 struct __align__(16) WarpSmem {
     RecF stage[2][PK_CH];
-    float4 ea[GROUP], eb[GROUP];  // members' expanded boxes (sparse sweep)
-    uint2 rng[GROUP];             // members' own ranges (sorted positions)
-    uint32_t qg[GROUP];           // members' query index in the batch
+    MemberRec mem[GROUP];  // the tile's group members
+    RecF cbox[32];         // bounding records of the tile's chunks (arrays that have them)
     // exact-test queue, first in first out, carried from tile to tile: query index in the batch,
     // entry position in its sorted array, tile | sel << 29, query index within its request
     uint32_t q_qi[PK_QUEUE], q_pos[PK_QUEUE], q_tile[PK_QUEUE], q_ql[PK_QUEUE];
     unsigned long long bar[2];
+    unsigned long long mbar;  // members + chunk boxes
 };
 
 enum { PASS_COUNT = 0, PASS_WRITE = 1 };
@@ -514,11 +528,12 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
     if (lane == 0) {
         mbar_init(&W.bar[0], 1);
         mbar_init(&W.bar[1], 1);
+        mbar_init(&W.mbar, 1);
         fence_mbar_init();
     }
     __syncwarp();
-    uint32_t parity[2] = {0u, 0u};
-    bool pending[2] = {false, false};
+    uint32_t parity[2] = {0u, 0u}, mparity = 0u;
+    bool pending[2] = {false, false}, mpending = false;
     bool abort = false;
 
     uint64_t ntiles = (uint64_t)B.hdr[HDR_T_LO] | ((uint64_t)B.hdr[HDR_T_HI] << 32);
@@ -606,60 +621,74 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         wt_cur = last_tile;
     };
 
-    // tiles are taken from a device counter; the next index is fetched while a tile is swept
+    // tiles are taken from a device counter; the next index and its descriptor are fetched
+    // while a tile is swept
     uint64_t t = 0;
     if (lane == 0) t = atomicAdd(&B.counters[PASS], 1u);
     t = __shfl_sync(FULL, t, 0);
+    uint4 D = t < ntiles ? B.tdesc[t] : make_uint4(0u, 0u, 0u, 0u);
     while (!abort && t < ntiles) {
         uint64_t t_next = 0;
         if (lane == 0) t_next = atomicAdd(&B.counters[PASS], 1u);
         if (PASS == PASS_WRITE && B.tile_hits[t] == 0) {  // no rows in this tile
             t = __shfl_sync(FULL, t_next, 0);
+            D = t < ntiles ? B.tdesc[t] : make_uint4(0u, 0u, 0u, 0u);
             continue;
         }
-        const uint4 D = B.tdesc[t];
-        const uint32_t first = D.x, s0 = D.y, s1 = D.z;
+        const uint32_t g = D.x, s0 = D.y, s1 = D.z;
         const uint32_t sel = D.w & 7u, count = ((D.w >> 3) & 31u) + 1u, req = D.w >> 8;
         const uint32_t tw = (uint32_t)t | (sel << 29);
         const RecF *recs = P.rec[sel];
-        // the first two chunks of records are in flight while the members are loaded
+        const RecF *bx = P.box[sel];
         const uint32_t nrec = s1 - s0;
         const uint32_t nch = (nrec + PK_CH - 1) / PK_CH;
+        // one bulk copy of the members (and of the chunks' bounding records), then the first two
+        // chunks of records
         if (lane == 0) {
+            const uint32_t mb = count * (uint32_t)sizeof(MemberRec);
+            const uint32_t cb = bx ? nch * (uint32_t)sizeof(RecF) : 0u;
+            mbar_arrive_tx(&W.mbar, mb + cb);
+            bulk_g2s(&W.mem[0], B.gmem + (uint64_t)g * GROUP, mb, &W.mbar);
+            if (bx) bulk_g2s(&W.cbox[0], bx + s0 / PK_CH, cb, &W.mbar);
             for (uint32_t c = 0; c < 2 && c < nch; c++) {
                 const uint32_t cs = s0 + c * PK_CH, cn = min((uint32_t)PK_CH, s1 - cs);
                 mbar_arrive_tx(&W.bar[c], cn * (uint32_t)sizeof(RecF));
                 bulk_g2s(&W.stage[c][0], recs + cs, cn * (uint32_t)sizeof(RecF), &W.bar[c]);
             }
         }
+        mpending = true;
         pending[0] = nch > 0;
         pending[1] = nch > 1;
         // a group's members belong to one request: its d bounds for the gap filter
         const ReqDesc &RQ = P.reqs[req];
         const float d_dn = RQ.d_dn, d2u = RQ.d2u;
         const uint32_t q_first = RQ.q_first;
+        if (!mbar_wait_bounded(&W.mbar, mparity)) {
+            abort = true;
+            break;
+        }
+        mparity ^= 1u;
+        mpending = false;
+        // the next tile's descriptor is in flight during the sweep
+        uint4 Dn = make_uint4(0u, 0u, 0u, 0u);
+        if (lane == 0 && t_next < ntiles) Dn = B.tdesc[t_next];
 
         // members of the group: one per lane, their expanded boxes and ranges in registers
         uint32_t lo = 0, hi = 0, myq = 0;
         float4 ea = make_float4(0.f, 0.f, 0.f, 0.f), eb = ea;
         if ((uint32_t)lane < count) {
-            const uint32_t u = B.vals[first + lane];
-            myq = B.u_q[u];
-            lo = B.u_lo[u];
-            hi = B.u_hi[u];
-            if (B.u_sel[u] != sel) lo = hi = 0;
-            W.qg[lane] = myq;
-            ea = B.qf[2 * (uint64_t)myq + 0];
-            eb = B.qf[2 * (uint64_t)myq + 1];
-            W.ea[lane] = ea;
-            W.eb[lane] = eb;
-            W.rng[lane] = make_uint2(lo, hi);
+            const MemberRec &M = W.mem[lane];
+            myq = M.qi;
+            lo = M.lo;
+            hi = M.hi;
+            if (M.sel != sel) lo = hi = 0;
+            ea = M.ea;
+            eb = M.eb;
             if (PASS == PASS_COUNT) {
                 const uint32_t a = max(lo, s0), bnd = min(hi, s1);
                 acc_tests += bnd > a ? bnd - a : 0u;
             }
         }
-        __syncwarp();
         // the axis of the stage-1 sweep, the one on which the array's entries are least likely
         // to meet the query: time for grid cells (a cell holds entries of every time), y for an
         // X subbin (its entries overlap the query in x by construction), x otherwise
@@ -688,12 +717,11 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
 
         // the chunks this lane's member meets: its range overlaps the chunk and, for an array
         // with chunk boxes, its expanded box meets the chunk's bounding record
-        const RecF *bx = P.box[sel];
         uint32_t mc = 0u;
         for (uint32_t c = 0; c < nch; c++) {
             const uint32_t cs = s0 + c * PK_CH, ce = min(cs + (uint32_t)PK_CH, s1);
             bool meet = lo < ce && hi > cs;
-            if (bx && meet) meet = filter_box(bx[cs / PK_CH], ea, eb);
+            if (bx && meet) meet = filter_box(W.cbox[c], ea, eb);
             mc |= (uint32_t)meet << c;
         }
         // chunks to sweep, in order; the first two were copied already, later ones are copied
@@ -737,13 +765,13 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 if (!in1) r1.t0 = INFINITY;
                 const uint32_t pos0 = cs + lane, pos1 = cs + 32 + lane;
                 for (unsigned rem = act; rem; rem &= rem - 1u) {
-                    const uint32_t m = __ffs(rem) - 1;
-                    const uint2 rg = W.rng[m];
-                    const float4 mea = W.ea[m], meb = W.eb[m];
-                    const uint32_t mq = W.qg[m];
-                    const uint32_t w = rg.y - rg.x;
-                    bool p0 = (pos0 - rg.x) < w && filter_box(r0, mea, meb);
-                    bool p1 = (pos1 - rg.x) < w && filter_box(r1, mea, meb);
+                    // (a member in act has this tile's array: its range is its own)
+                    const MemberRec &M = W.mem[__ffs(rem) - 1];
+                    const float4 mea = M.ea, meb = M.eb;
+                    const uint32_t mq = M.qi, mlo = M.lo;
+                    const uint32_t w = M.hi - mlo;
+                    bool p0 = (pos0 - mlo) < w && filter_box(r0, mea, meb);
+                    bool p1 = (pos1 - mlo) < w && filter_box(r1, mea, meb);
                     p0 = p0 && filter_gap_e(r0, mea, meb, d_dn, d2u);
                     p1 = p1 && filter_gap_e(r1, mea, meb, d_dn, d2u);
                     enqueue(p0, mq, pos0);
@@ -798,6 +826,10 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         }
         __syncwarp();
         t = __shfl_sync(FULL, t_next, 0);
+        D.x = __shfl_sync(FULL, Dn.x, 0);
+        D.y = __shfl_sync(FULL, Dn.y, 0);
+        D.z = __shfl_sync(FULL, Dn.z, 0);
+        D.w = __shfl_sync(FULL, Dn.w, 0);
     }
     if (!abort && qn) {
         __syncwarp();
@@ -808,6 +840,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         // let copies still in flight land before the shared memory is released
         for (int st = 0; st < 2; st++)
             if (pending[st]) mbar_wait_bounded(&W.bar[st], parity[st]);
+        if (mpending) mbar_wait_bounded(&W.mbar, mparity);
     }
     if (PASS == PASS_COUNT) {
         for (int o = 16; o; o >>= 1) acc_tests += __shfl_xor_sync(FULL, acc_tests, o);
@@ -1151,7 +1184,7 @@ namespace {
 // Work buffers of a plain search, allocated stage by stage at their exact sizes.
 struct PlainWork {
     DevBuf qd, qf, qreq, qcell, qnu, quoff, u_q, u_lo, u_hi, u_sel, keys, vals, req, groups, segs,
-        ntiles, tile_base, tiles, tdesc, tile_off, ctl, reqdesc, scratch;
+        ntiles, tile_base, tiles, tdesc, tile_off, ctl, reqdesc, scratch, gmem;
 };
 
 ts_status alloc_units(PlainWork &w, PipeBufs &b, uint64_t units, cudaStream_t s)
@@ -1226,6 +1259,8 @@ ts_status plain_prepare(const Index *ix, const double *const cols[8], uint64_t n
     if (!group) return TS_OK;
     c.groups = (units + GROUP - 1) / GROUP + 1;
     TS_CHECK(w.groups.alloc(sizeof(uint32_t) * 3 * c.groups, s));
+    TS_CHECK(w.gmem.alloc(sizeof(MemberRec) * GROUP * c.groups, s));
+    b.gmem = w.gmem.as<MemberRec>();
     TS_CHECK(w.segs.alloc(sizeof(uint32_t) * 4 * GROUP * c.groups, s));
     TS_CHECK(w.ntiles.alloc(sizeof(uint32_t) * c.groups, s));
     TS_CHECK(w.tile_base.alloc(sizeof(uint64_t) * (c.groups + 1), s));

@@ -24,7 +24,7 @@ constexpr uint32_t PK_MAX_TILES = (1u << 29) - 1;  // tile index bits of a queue
 constexpr int PK_SPARSE = 8;  // chunks met by at most this many members: per-member sweep
 constexpr int PK_TILE = 256;   // records per tile (multiple of PK_CH)
 constexpr int GROUP = 32;      // units per group
-constexpr int PK_MIN_BLOCKS = 3;  // resident pair-kernel blocks per SM the register budget targets
+constexpr int PK_MIN_BLOCKS = 2;  // resident pair-kernel blocks per SM the register budget targets
 
 // run header words: valid units, groups, tiles (low, high), unit slots holding a sort key
 enum { HDR_U = 0, HDR_G = 1, HDR_T_LO = 2, HDR_T_HI = 3, HDR_NU = 4, HDR_N = 5 };
@@ -37,6 +37,15 @@ struct ReqDesc {
     float d_dn, pad;            // FP32 lower bound of d
     const double *cols[8];      // batched runs: the request's query columns (device-readable)
 };
+
+// A group member as the pair kernel reads it (one bulk copy per tile): the query's d-expanded
+// FP32 box (with its clipped window), the unit's own range in its array, the query index in the
+// batch and the array.
+struct __align__(16) MemberRec {
+    float4 ea, eb;
+    uint32_t lo, hi, qi, sel;
+};
+static_assert(sizeof(MemberRec) == 48, "MemberRec is 48 bytes");
 
 // Device buffers of one pipeline run (pointers; ownership outside).
 struct PipeBufs {
@@ -55,12 +64,12 @@ struct PipeBufs {
     uint32_t *req_units, *ustart, *req_groups, *gstart;  // R, R+1, R, R+1
     // groups
     uint32_t *g_first, *g_count, *g_nseg;
+    MemberRec *gmem;      // GROUP per group, in the group's (array, start) order
     uint32_t *seg_lo, *seg_hi, *seg_sel, *seg_t0;  // GROUP per group
     uint32_t *ntiles;
     uint64_t *tile_base;  // groups + 1
     // tiles and rows
-    uint4 *tdesc;         // per tile: {first member (sorted unit slot), s0, s1,
-                          //            sel | (members - 1) << 3 | request << 8}
+    uint4 *tdesc;         // per tile: {group, s0, s1, sel | (members - 1) << 3 | request << 8}
     uint32_t *tile_hits;
     uint64_t *tile_off;   // tiles + 1
     uint32_t *out_q, *out_e;
