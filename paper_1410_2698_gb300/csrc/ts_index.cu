@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "ts_index.cuh"
 
@@ -450,6 +451,18 @@ void destroy_index(Index *ix)
     delete ix;
 }
 
+// Boundary table lo + j*w (j = 0..v) of a partition, evaluated exactly as part_bound does.
+static ts_status upload_bounds(Index *ix, double **dst, double lo, double w, uint32_t v,
+                               cudaStream_t s)
+{
+    std::vector<double> h(v + 1);
+    for (uint32_t j = 0; j <= v; j++) h[j] = part_bound(lo, w, (int)j);
+    TS_CHECK(ix->alloc(dst, v + 1));
+    TS_CUDA(cudaMemcpyAsync(*dst, h.data(), sizeof(double) * (v + 1), cudaMemcpyHostToDevice, s));
+    TS_CUDA(cudaStreamSynchronize(s));
+    return TS_OK;
+}
+
 ts_status build_index(const ts_segments *db, const ts_index_params *p, cudaStream_t s,
                       Index **out)
 {
@@ -626,6 +639,8 @@ ts_status build_index(const ts_segments *db, const ts_index_params *p, cudaStrea
                 ix->v[d] = (uint32_t)v;
                 ix->sub_lo[d] = ix->emin[d];
                 ix->sub_w[d] = ext / (double)ix->v[d];
+                TS_CHECK(upload_bounds(ix, &ix->sub_bound[d], ix->sub_lo[d], ix->sub_w[d],
+                                       ix->v[d], s));
                 TS_CHECK(build_st_dim(c, ix, d, lo3.as<double>() + d * n, hi3.as<double>() + d * n,
                                       bin_of.as<uint32_t>()));
             }
@@ -635,6 +650,7 @@ ts_status build_index(const ts_segments *db, const ts_index_params *p, cudaStrea
             for (int d = 0; d < 3; d++) {
                 ix->g_lo[d] = ix->emin[d];
                 ix->g_w[d] = (ix->emax[d] - ix->emin[d]) / (double)g;
+                TS_CHECK(upload_bounds(ix, &ix->g_bound[d], ix->g_lo[d], ix->g_w[d], g, s));
             }
             TS_CHECK(build_grid(c, ix, lo3.as<double>(), hi3.as<double>()));
         }

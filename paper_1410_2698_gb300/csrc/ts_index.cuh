@@ -45,6 +45,7 @@ struct Index {
     uint32_t *st_ids[3] = {nullptr, nullptr, nullptr};
     RecF *st_rec[3] = {nullptr, nullptr, nullptr};
     uint32_t *st_off[3] = {nullptr, nullptr, nullptr};
+    double *sub_bound[3] = {nullptr, nullptr, nullptr};  // lo + j*w for j = 0..v
     uint64_t st_len[3] = {0, 0, 0};
 
     // flatly structured grid (Sec. 4.1), one cell per entry (the cell of its MBB's minimum
@@ -55,6 +56,7 @@ struct Index {
     uint32_t *ga = nullptr;
     RecF *ga_rec = nullptr;
     uint32_t *g_off = nullptr;  // g^3 + 1
+    double *g_bound[3] = {nullptr, nullptr, nullptr};  // lo + j*w for j = 0..g
     uint64_t g_len = 0;
 
     size_t bytes = 0;

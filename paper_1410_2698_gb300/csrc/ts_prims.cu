@@ -393,6 +393,83 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K *keys_in, con
     }
 }
 
+// Scatter of one pass that computes its own digit offsets from the per-tile histograms (for at
+// most RS_FUSED_TILES tiles): thread d adds up digit d over all tiles and over the tiles before
+// this block's, and a block scan over the digit totals gives every digit's first position.
+constexpr uint32_t RS_FUSED_TILES = 256;
+
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter_fused(const K *keys_in,
+                                                                 const uint32_t *vals_in,
+                                                                 K *keys_out, uint32_t *vals_out,
+                                                                 uint64_t ncap, const uint32_t *n_dev,
+                                                                 int shift, const uint32_t *hist,
+                                                                 uint32_t ntiles)
+{
+    __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
+    __shared__ uint32_t dbase[RS_RADIX];
+    const uint64_t n = dev_count(ncap, n_dev);
+    if ((uint64_t)blockIdx.x * RS_TILE >= n) return;
+    {
+        const int d = threadIdx.x;  // RS_THREADS == RS_RADIX
+        uint32_t tot = 0, pre = 0;
+        for (uint32_t t = 0; t < ntiles; t++) {
+            const uint32_t v = hist[(uint64_t)d * ntiles + t];
+            tot += v;
+            pre += t < blockIdx.x ? v : 0u;
+        }
+        uint32_t all;
+        const uint32_t base = block_excl_scan<uint32_t>(tot, &all);
+        dbase[d] = base + pre;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * RS_RADIX; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t wbase = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)wid * (RS_ITEMS * 32);
+    K key[RS_ITEMS];
+    uint32_t val[RS_ITEMS];
+    uint32_t rank[RS_ITEMS];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; k++) {
+        uint64_t i = wbase + (uint64_t)k * 32 + lane;
+        bool ok = i < n;
+        key[k] = ok ? keys_in[i] : K(0);
+        val[k] = ok ? vals_in[i] : 0u;
+        uint32_t dgt = ok ? ((uint32_t)(key[k] >> shift) & 0xffu) : 0x100u;
+        uint32_t peers = __match_any_sync(0xffffffffu, dgt);
+        uint32_t before = __popc(peers & lt_mask);
+        uint32_t leader = __ffs(peers) - 1;
+        uint32_t cur = 0;
+        if (ok && lane == (int)leader) {
+            cur = wcnt[wid][dgt];
+            wcnt[wid][dgt] = cur + __popc(peers);
+        }
+        cur = __shfl_sync(0xffffffffu, cur, leader);
+        rank[k] = cur + before;
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int dgt = threadIdx.x; dgt < RS_RADIX; dgt += RS_THREADS) {
+        uint32_t run = 0;
+        for (int w = 0; w < RS_WARPS; w++) {
+            uint32_t c = wcnt[w][dgt];
+            wcnt[w][dgt] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; k++) {
+        uint64_t i = wbase + (uint64_t)k * 32 + lane;
+        if (i >= n) continue;
+        uint32_t dgt = (uint32_t)(key[k] >> shift) & 0xffu;
+        uint64_t dst = (uint64_t)dbase[dgt] + wcnt[wid][dgt] + rank[k];
+        keys_out[dst] = key[k];
+        vals_out[dst] = val[k];
+    }
+}
+
 template <class K>
 __global__ void k_copy_kv(const K *ks, const uint32_t *vs, K *kd, uint32_t *vd, uint64_t ncap,
                           const uint32_t *n_dev)
@@ -416,7 +493,8 @@ static ts_status radix_sort_impl(K *keys, uint32_t *vals, uint64_t n, int bits, 
     TS_CHECK(vb.alloc(sizeof(uint32_t) * n, s));
     uint64_t nh = (uint64_t)RS_RADIX * ntiles;
     TS_CHECK(hist.alloc(sizeof(uint32_t) * nh, s));
-    TS_CHECK(off.alloc(sizeof(uint64_t) * (nh + 1), s));
+    const bool fused = ntiles <= RS_FUSED_TILES && n < (1ull << 32);
+    if (!fused) TS_CHECK(off.alloc(sizeof(uint64_t) * (nh + 1), s));
     K *ka = keys, *kbp = kb.as<K>();
     uint32_t *va = vals, *vbp = vb.as<uint32_t>();
     int passes = (bits + 7) / 8;
@@ -425,9 +503,14 @@ static ts_status radix_sort_impl(K *keys, uint32_t *vals, uint64_t n, int bits, 
         k_rs_hist<K><<<ntiles, RS_THREADS, 0, s>>>(ka, n, n_dev, shift, hist.as<uint32_t>(),
                                                    ntiles);
         TS_LAUNCHED();
-        TS_CHECK(scan_u32_to_u64(hist.as<uint32_t>(), off.as<uint64_t>(), nh, s));
-        k_rs_scatter<K><<<ntiles, RS_THREADS, 0, s>>>(ka, va, kbp, vbp, n, n_dev, shift,
-                                                      off.as<uint64_t>(), ntiles);
+        if (fused) {
+            k_rs_scatter_fused<K><<<ntiles, RS_THREADS, 0, s>>>(ka, va, kbp, vbp, n, n_dev, shift,
+                                                                hist.as<uint32_t>(), ntiles);
+        } else {
+            TS_CHECK(scan_u32_to_u64(hist.as<uint32_t>(), off.as<uint64_t>(), nh, s));
+            k_rs_scatter<K><<<ntiles, RS_THREADS, 0, s>>>(ka, va, kbp, vbp, n, n_dev, shift,
+                                                          off.as<uint64_t>(), ntiles);
+        }
         TS_LAUNCHED();
         K *tk = ka; ka = kbp; kbp = tk;
         uint32_t *tv = va; va = vbp; vbp = tv;

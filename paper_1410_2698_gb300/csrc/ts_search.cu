@@ -69,6 +69,52 @@ __device__ __forceinline__ uint32_t first_pmax_above(const double *pmax, uint32_
     return lo;
 }
 
+// The part of x (as part_of) from the partition's boundary table bd[j] = lo + j*w: a first guess
+// in FP32 (iwf ~ 1/w; 0 when w = 0), corrected by the exact FP64 boundary comparisons, so the
+// result equals part_of's.
+__device__ __forceinline__ int part_of_t(double x, const double *bd, float iwf, int v)
+{
+    const double lo = bd[0];
+    if (!(x >= lo)) return -1;
+    if (v <= 1 || iwf == 0.0f) return v - 1;
+    const float f = floorf((float)(x - lo) * iwf);
+    int j = !(f < (float)v) ? v - 1 : (f < 0.0f ? 0 : (int)f);
+    while (j + 1 < v && bd[j + 1] <= x) j++;
+    while (j > 0 && bd[j] > x) j--;
+    return j;
+}
+
+// First bin whose prefix maximum of B^end exceeds w0 (as first_pmax_above), searched in a bracket:
+// pmax[j] >= B^start_{j+1} for every bin, so the answer is at most the bin holding w0 (jw); and
+// since an entry lasts at most max_dur, bins more than `back` before jw are checked with one load
+// (pmax[lo - 1] <= w0 keeps the answer at or after lo), otherwise the whole range is searched.
+__device__ __forceinline__ uint32_t first_pmax_above_b(const double *pmax, const double *bs,
+                                                       uint32_t m, float iwf, uint32_t back,
+                                                       double w0)
+{
+    const int jw = part_of_t(w0, bs, iwf, (int)m);
+    if (jw < 0) return first_pmax_above(pmax, 1, w0);  // before every bin: 0 or (m = 1) 1
+    uint32_t hi = (uint32_t)jw + 1 < m ? (uint32_t)jw + 1 : m;
+    uint32_t lo = (uint32_t)jw > back ? (uint32_t)jw - back : 0u;
+    if (lo > 0 && pmax[lo - 1] > w0) lo = 0;
+    // the answer lies in [lo, hi]; hi = m means no bin
+    if (hi == m && !(pmax[m - 1] > w0)) return m;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (pmax[mid] > w0) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// last bin with start < w1, or -1 (the table lookup, then the strict comparison)
+__device__ __forceinline__ int last_start_below_t(const double *bs, uint32_t m, float iwf,
+                                                  double w1)
+{
+    int j = part_of_t(w1, bs, iwf, (int)m);
+    while (j >= 0 && !(bs[j] < w1)) j--;
+    return j;
+}
+
 // last bin with start < w1, or -1
 __device__ __forceinline__ int last_start_below(const double *bs, uint32_t m, double w1)
 {
@@ -96,11 +142,16 @@ struct PrepParams {
     double tmin, tmax;
     const double *bin_start, *bin_pmax;
     const uint32_t *bin_off;
+    float bin_iwf;      // ~ 1 / bin width (first guesses only)
+    uint32_t bin_back;  // bins an entry can reach back (from its duration), plus a margin
     uint32_t v[3];
-    double sub_lo[3], sub_w[3], sub_iw[3];  // iw: reciprocal of the width
+    const double *sub_bound[3];  // subbin boundary tables (v + 1 each)
+    float sub_iwf[3];
     const uint32_t *st_off[3];
     uint32_t g;
-    double g_lo[3], g_w[3], g_iw[3], longest[3];
+    const double *g_bound[3];    // grid boundary tables (g + 1 each)
+    float g_iwf[3];
+    double g_lo[3], g_w[3], longest[3];
     PipeBufs b;
 };
 
@@ -170,8 +221,8 @@ __global__ void k_qprep(PrepParams P)
                 double a = ((mn[d] - R.d) - P.longest[d]) -
                            EXT_SLACK * ((fabs(mn[d]) + R.d) + P.longest[d]);
                 double bb = (mx[d] + R.d) + EXT_SLACK * (fabs(mx[d]) + R.d);
-                int pa = part_of_r(a, P.g_lo[d], P.g_w[d], P.g_iw[d], (int)P.g);
-                int pb = part_of_r(bb, P.g_lo[d], P.g_w[d], P.g_iw[d], (int)P.g);
+                int pa = part_of_t(a, P.g_bound[d], P.g_iwf[d], (int)P.g);
+                int pb = part_of_t(bb, P.g_bound[d], P.g_iwf[d], (int)P.g);
                 if (pa < 0) pa = 0;
                 if (pb < pa) any = false;
                 ca[d] = (uint32_t)pa;
@@ -186,8 +237,9 @@ __global__ void k_qprep(PrepParams P)
                     hi = (uint32_t)P.n;
                 } else {
                     // temporal range (Sec. 4.2 schedule)
-                    const uint32_t jl = first_pmax_above(P.bin_pmax, P.m, q.w0);
-                    const int jh = last_start_below(P.bin_start, P.m, q.w1);
+                    const uint32_t jl = first_pmax_above_b(P.bin_pmax, P.bin_start, P.m,
+                                                           P.bin_iwf, P.bin_back, q.w0);
+                    const int jh = last_start_below_t(P.bin_start, P.m, P.bin_iwf, q.w1);
                     const bool any = (int)jl <= jh;
                     if (any) {
                         lo = P.bin_off[jl];
@@ -202,9 +254,8 @@ __global__ void k_qprep(PrepParams P)
                             const int vv = (int)P.v[d];
                             double a = (mn[d] - R.d) - EXT_SLACK * (fabs(mn[d]) + R.d);
                             double bb = (mx[d] + R.d) + EXT_SLACK * (fabs(mx[d]) + R.d);
-                            const double iw = P.sub_iw[d];
-                            const int pa = part_of_r(a, P.sub_lo[d], P.sub_w[d], iw, vv);
-                            const int pb = part_of_r(bb, P.sub_lo[d], P.sub_w[d], iw, vv);
+                            const int pa = part_of_t(a, P.sub_bound[d], P.sub_iwf[d], vv);
+                            const int pb = part_of_t(bb, P.sub_bound[d], P.sub_iwf[d], vv);
                             const int ja = pa < 0 ? 0 : pa, jb = pb;
                             uint32_t clo, chi;
                             if (jb < ja) {
@@ -1026,15 +1077,20 @@ ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq
     P.bin_start = ix->bin_start;
     P.bin_pmax = ix->bin_pmax;
     P.bin_off = ix->bin_off;
+    P.bin_iwf = ix->b > 0.0 ? (float)(1.0 / ix->b) : 0.0f;
+    {
+        const double back = ix->b > 0.0 ? ceil(ix->max_dur / ix->b) + 2.0 : (double)ix->m;
+        P.bin_back = back < (double)ix->m ? (uint32_t)back : ix->m;
+    }
     for (int d = 0; d < 3; d++) {
         P.v[d] = ix->v[d];
-        P.sub_lo[d] = ix->sub_lo[d];
-        P.sub_w[d] = ix->sub_w[d];
-        P.sub_iw[d] = ix->sub_w[d] > 0.0 ? 1.0 / ix->sub_w[d] : 0.0;
+        P.sub_bound[d] = ix->sub_bound[d];
+        P.sub_iwf[d] = ix->sub_w[d] > 0.0 ? (float)(1.0 / ix->sub_w[d]) : 0.0f;
         P.st_off[d] = ix->st_off[d];
+        P.g_bound[d] = ix->g_bound[d];
+        P.g_iwf[d] = ix->g_w[d] > 0.0 ? (float)(1.0 / ix->g_w[d]) : 0.0f;
         P.g_lo[d] = ix->g_lo[d];
         P.g_w[d] = ix->g_w[d];
-        P.g_iw[d] = ix->g_w[d] > 0.0 ? 1.0 / ix->g_w[d] : 0.0;
         P.longest[d] = ix->longest[d];
     }
     P.g = ix->g;
