@@ -47,10 +47,14 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="records per work tile (0 = default)")
     ap.add_argument("--pair-blocks", type=int, default=0, help="pair kernel blocks (0 = all)")
+    ap.add_argument("--serial-plans", action="store_true",
+                    help="one batch plan at a time (automatic when the plans would not fit)")
     ap.add_argument("--served-index", default="spatiotemporal")
     ap.add_argument("--served-requests", type=int, default=200)
     ap.add_argument("--served-max-traj", type=int, default=500)
     ap.add_argument("--served-rho", type=float, default=0.9)
+    ap.add_argument("--served-only", action="store_true",
+                    help="only the served form (its own JSON line) on the workload's database")
     return ap.parse_args()
 
 
@@ -234,28 +238,53 @@ def run_gpu(args):
         plain_step(warm)
     rows_per_batch = {k: sum(st["n_hits"] for kk, _, st in warm if kk == k) // max(args.warmup, 1)
                       for k in kinds}
+    # a batch's tiles are its requests' tiles (one request per d)
+    tiles_per_batch = {k: sum(st["n_tiles"] for kk, _, st in warm if kk == k) //
+                       max(args.warmup, 1) for k in kinds}
     # batched form: one reusable plan per index, replayed as a CUDA graph; the distances are the
     # requests of one batch
     reqs = [(qdev, d, w.t_start, w.t_end) for d in w.distances]
-    plans = {k: api.BatchPlan(indexes[k], max_requests=len(reqs),
-                              max_queries=w.queries.n * len(reqs),
-                              max_rows=max(1 << 20, 2 * rows_per_batch[k]), use_graph=True,
-                              stream=0, tile_records=args.tile, pair_blocks=args.pair_blocks)
-             for k in kinds}
+    # a plan holds its rows (24 B) and the count pass's kept hits (32 B) for max_rows rows
+    plan_bytes = sum(56 * max(1 << 20, 2 * rows_per_batch[k]) for k in kinds)
+    serial = args.serial_plans or plan_bytes > 60e9
+
+    # grid plans hold one unit per z-run of a query's cells: their count from the schedule
+    units = {}
+    for k in kinds:
+        if k == "spatial":
+            units[k] = sum(int(api.ts_schedule(indexes[k], w.queries, d, w.t_start,
+                                               w.t_end)[1].sum()) for d in w.distances)
+            units[k] += units[k] // 10 + 1024
+        else:
+            units[k] = 0  # one unit per query (the plan's default)
+
+    def make_plan(k, own_stream):
+        rows = (rows_per_batch[k] + rows_per_batch[k] // 20 + (1 << 20)) if serial else \
+            max(1 << 20, 2 * rows_per_batch[k])
+        return api.BatchPlan(indexes[k], max_requests=len(reqs),
+                             max_queries=w.queries.n * len(reqs), max_rows=rows, use_graph=True,
+                             stream=0 if own_stream else None, tile_records=args.tile,
+                             pair_blocks=args.pair_blocks, max_units=units[k],
+                             max_tiles=tiles_per_batch[k] + tiles_per_batch[k] // 10 + 65536)
+
     batch_stats = []
+    alone = []
+    plans = {}
+    if not serial:
+        plans = {k: make_plan(k, True) for k in kinds}
 
-    def batched_step(collect=None):
-        for k in kinds:
-            plans[k].run(reqs, stream=0)  # each plan on its own stream: the plans overlap
-        for k in kinds:
-            st = plans[k].wait()
-            if st["overflow"]:
-                raise RuntimeError(f"batch plan overflow for {k}")
-            if collect is not None:
-                collect.append((k, st))
+        def batched_step(collect=None):
+            for k in kinds:
+                plans[k].run(reqs, stream=0)  # each plan on its own stream: the plans overlap
+            for k in kinds:
+                st = plans[k].wait()
+                if st["overflow"]:
+                    raise RuntimeError(f"batch plan overflow for {k}")
+                if collect is not None:
+                    collect.append((k, st))
 
-    for _ in range(max(args.warmup, 0)):
-        batched_step()
+        for _ in range(max(args.warmup, 0)):
+            batched_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -265,18 +294,45 @@ def run_gpu(args):
     per = []
     plain_ms = _timed(args, stream, flush, lambda: plain_step(per))
     l1 = api.ts_kernel_launches()
-    batch_ms = _timed(args, stream, flush, lambda: batched_step(batch_stats))
-    l2 = api.ts_kernel_launches()
-    # the pair kernel timed alone: the same plans, one at a time on the bench stream (in the
-    # overlapped step the events of one plan also see the other plans' kernels)
-    alone = []
+    if not serial:
+        batch_ms = _timed(args, stream, flush, lambda: batched_step(batch_stats))
+        l2 = api.ts_kernel_launches()
 
-    def alone_step():
+        # the pair kernel timed alone: the same plans, one at a time on the bench stream (in
+        # the overlapped step the events of one plan also see the other plans' kernels)
+        def alone_step():
+            for k in kinds:
+                plans[k].run(reqs)
+                alone.append((k, plans[k].wait()))
+
+        alone_ms = _timed(args, stream, flush, alone_step, steps=min(args.steps, 20))
+    else:
+        # one plan at a time (setup outside the timed region): a step's time is the sum of the
+        # indexes' step times
+        batch_ms = [0.0] * args.steps
+        launched = 0
         for k in kinds:
-            plans[k].run(reqs)
-            alone.append((k, plans[k].wait()))
+            plan = make_plan(k, False)
 
-    alone_ms = _timed(args, stream, flush, alone_step, steps=min(args.steps, 20))
+            def one(plan=plan, k=k):
+                plan.run(reqs)
+                st = plan.wait()
+                if st["overflow"]:
+                    raise RuntimeError(f"batch plan overflow for {k}")
+                batch_stats.append((k, st))
+
+            for _ in range(max(args.warmup, 0)):
+                plan.run(reqs)
+                plan.wait()
+            n0 = len(batch_stats)
+            a = api.ts_kernel_launches()
+            for i, v in enumerate(_timed(args, stream, flush, one)):
+                batch_ms[i] += v
+            launched += api.ts_kernel_launches() - a
+            alone.extend(batch_stats[n0:])
+            plan.free()
+        l2 = l1 + launched
+        alone_ms = batch_ms
     torch.cuda.synchronize()
     clk = clocks.stop()
     plain_total = _max_over_ranks(float(sum(plain_ms)), world, dev)
@@ -359,8 +415,12 @@ def run_gpu(args):
                   "form": "one ts_search per index and d"},
         "breakdown": breakdown,
     }
+    line["config"]["plans"] = "one at a time" if serial else "resident together, overlapped"
     if not args.no_e2e:
-        line["e2e"] = run_e2e(args, api, w, plans, kinds)
+        if serial:
+            line["e2e"] = run_e2e(args, api, w, None, kinds, make_plan)
+        else:
+            line["e2e"] = run_e2e(args, api, w, plans, kinds)
     if not args.no_served and rank == 0:
         sk = args.served_index
         sidx = indexes[sk] if sk in indexes else api.ts_build_index(w.db, kind=sk)
@@ -379,12 +439,36 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, api, w, plans, kinds):
+def run_e2e(args, api, w, plans, kinds, make_plan=None):
     """The batched step through the C ABI with HOST buffers: the query columns are staged from
     host memory and every result row is copied to host memory inside the timed region (wall
-    clock, the stream synchronised on both sides)."""
+    clock, the stream synchronised on both sides). With make_plan (plans that do not fit
+    together) each index's plan is created, timed over the steps and released in turn."""
     import torch
     reqs = [(w.queries, d, w.t_start, w.t_end) for d in w.distances]
+    if make_plan is not None:
+        total_ms, h2d, d2h, qsegs = 0.0, 0, 0, 0
+        steps = max(1, min(args.steps, 5))
+        for k in kinds:
+            plan = make_plan(k, False)
+            plan.run(reqs)
+            plan.wait()  # warm-up
+            for _ in range(steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                plan.run(reqs)
+                st = plan.wait()
+                for r in range(len(reqs)):
+                    rows = plan.request_to_host(r)
+                    d2h += sum(v.nbytes for v in rows.values())
+                torch.cuda.synchronize()
+                total_ms += (time.perf_counter() - t0) * 1e3
+                qsegs += st["stats"]["n_qsegs"]
+                h2d += 8 * 8 * w.queries.n * len(reqs)
+            plan.free()
+        return {"value": qsegs / (total_ms / 1e3), "unit": "query segs/s",
+                "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
+                "steps": steps}
     ms = []
     h2d = d2h = qsegs = 0
     for s in range(args.steps + 1):
@@ -429,18 +513,20 @@ def run_served(args, api, w, index):
     # plain: one synchronous search per request (after two warm-up searches)
     for r in stream[:2]:
         api.ts_search(index, r.queries, r.d, r.t_start, r.t_end).free()
-    lat_plain, rows_plain = [], 0
+    lat_plain, rows_plain, max_rows = [], 0, 0
     t0 = time.perf_counter()
     for r in stream:
         a = time.perf_counter()
         res = api.ts_search(index, r.queries, r.d, r.t_start, r.t_end)
         rows_plain += res.count
+        max_rows = max(max_rows, res.count)
         res.free()
         lat_plain.append((time.perf_counter() - a) * 1e3)
     plain_s = time.perf_counter() - t0
     mu_plain = len(stream) / plain_s
     srv = api.Server(index, max_batch_requests=64, max_batch_queries=max(1 << 20, 2 * max_q),
-                     max_batch_rows=1 << 25, max_inflight=2, use_graph=True, linger_us=200)
+                     max_batch_rows=max(1 << 25, 2 * max_rows), max_inflight=2, use_graph=True,
+                     linger_us=200)
     try:
         def serve(arrivals):
             tickets = [None] * len(stream)
@@ -483,6 +569,7 @@ def run_served(args, api, w, index):
         "workload": f"{len(stream)} requests of 1-{args.served_max_traj} query trajectory runs "
                     f"(log-uniform) of 10-200 segments, interval = the runs' span, d log-uniform "
                     f"in [0.5, 10]; query arrays on the host",
+        "max_request_rows": max_rows,
         "plain": {"qsegs_per_s": qsegs / plain_s, "req_per_s": mu_plain,
                   "p50_ms": _pct(lat_plain, 50), "p99_ms": _pct(lat_plain, 99)},
         "saturated": {"qsegs_per_s": qsegs / sat_s, "req_per_s": len(stream) / sat_s,
@@ -566,10 +653,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_served_only(args):
+    """The served form alone on the workload's database: one JSON line (rank 0)."""
+    import torch
+    from paper_1410_2698_gb300 import api
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    w = load_workload(args.workload, 0)
+    idx = api.ts_build_index(w.db, kind=args.served_index)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    served = run_served(args, api, w, idx)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": served["saturated"]["qsegs_per_s"], "unit": "query segs/s",
+            "n_gpus": 1, "form": "served (saturated); plain and Poisson beside it",
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.db.n} db segments (resident), "
+                                   f"{args.served_index} index; " + served["workload"]},
+            "clocks": clk, "served": served}
+    print(json.dumps(line), flush=True)
+    idx.free()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.served_only:
+        run_served_only(args)
     else:
         run_gpu(args)
 

@@ -214,7 +214,7 @@ typedef struct ts_batch_params {
     int32_t pair_blocks;    /* blocks of the persistent pair kernel (0 = all resident) */
     uint64_t scratch_rows;  /* hits the count pass keeps (32 B each) and places after the scan;
                                a run with more hits sweeps its tiles a second time to write them
-                               (0 = min(max_rows, 2^24)) */
+                               (0 = max_rows) */
 } ts_batch_params;
 
 typedef struct ts_batch ts_batch;
@@ -264,11 +264,15 @@ typedef struct ts_server_params {
     uint32_t max_inflight;        /* batches on the device at once (>= 1; 2 overlaps batches) */
     uint32_t max_batch_requests;  /* requests per batch */
     uint64_t max_batch_queries;   /* query segments per batch (admission capacity) */
-    uint64_t max_batch_rows;      /* result rows per batch (admission capacity) */
+    uint64_t max_batch_rows;      /* result rows of a batch: its count pass sizes the rows
+                                     exactly; a batch with more is split, a lone request with
+                                     more ends with TS_ERR_CAPACITY */
     uint32_t tile_records;        /* as in ts_batch_params */
     int32_t use_graph;            /* replay each batch plan as a CUDA graph */
     uint32_t linger_us;           /* how long a partly filled batch waits for more requests */
     uint32_t reserved;
+    uint64_t scratch_rows;        /* hits a batch's count pass keeps for placement (0 = 2^24);
+                                     a batch with more sweeps its tiles a second time */
 } ts_server_params;
 
 typedef struct ts_server ts_server;

@@ -385,11 +385,13 @@ ts_status ts_server_wait(ts_server *h, uint64_t ticket, uint32_t timeout_ms, ts_
     *out = nullptr;
     return guarded([&]() -> ts_status {
         SearchOut o;
-        ts_status st = server_wait(s, ticket, timeout_ms, &o, timing);
+        std::shared_ptr<RowBlock> block;
+        ts_status st = server_wait(s, ticket, timeout_ms, &o, &block, timing);
         if (st != TS_OK) return st;
         ts_result *r = new ts_result();
         r->stream = nullptr;
         r->out = o;
+        r->block = block;
         *out = r;
         return clear_error(TS_OK);
     });

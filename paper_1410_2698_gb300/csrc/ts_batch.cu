@@ -179,14 +179,13 @@ ts_status create_plan(const Index *ix, const ts_batch_params *prm, cudaStream_t 
     const bool grid = ix->kind == TS_INDEX_SPATIAL;
     k.units = prm->max_units ? prm->max_units : (grid ? 16 * k.nq : k.nq);
     k.groups = k.units / GROUP + k.nreq + 1;
-    k.tiles = prm->max_tiles ? prm->max_tiles : 64 * k.groups + 65536;
+    k.tiles = prm->max_tiles ? prm->max_tiles : 256 * k.groups + 65536;  // 28 B per tile
     k.rows = own_rows ? prm->max_rows : ~0ull;
     // hits the count pass keeps for placement after the scan; more hits than this make the
     // write pass sweep the tiles again
-    k.scratch = prm->scratch_rows
-                    ? prm->scratch_rows
-                    : std::min<uint64_t>(own_rows ? prm->max_rows : 4 * k.nq + (1ull << 20),
-                                         SCRATCH_MAX);
+    k.scratch = prm->scratch_rows ? prm->scratch_rows
+                : own_rows       ? prm->max_rows
+                                 : std::min<uint64_t>(4 * k.nq + (1ull << 20), SCRATCH_MAX);
     Carver sz;
     layout(p.get(), sz);
     p->dbytes = sz.off;
@@ -343,7 +342,7 @@ ts_status plan_run(BatchPlan *p, uint32_t nreq, const ts_segments *qs, const ts_
             // kernels enqueued during the capture are counted once, for this first replay
             const unsigned long long before = launch_count();
             TS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            ts_status e = enqueue_run(p, st, true);
+            ts_status e = enqueue_run(p, st, p->own_rows);
             cudaGraph_t g = nullptr;
             cudaError_t ce = cudaStreamEndCapture(st, &g);
             if (e != TS_OK) {
@@ -359,7 +358,7 @@ ts_status plan_run(BatchPlan *p, uint32_t nreq, const ts_segments *qs, const ts_
         }
         TS_CUDA(cudaGraphLaunch(p->exec, st));
     } else {
-        TS_CHECK(enqueue_run(p, st, true));
+        TS_CHECK(enqueue_run(p, st, p->own_rows));
     }
     p->running = true;
     p->last_stream = st;
@@ -472,7 +471,7 @@ ts_status search_batch(const Index *ix, uint32_t nreq, const ts_segments *qs,
     }
     if (total) {
         block = std::make_shared<RowBlock>();
-        TS_CHECK(block->alloc(total));
+        TS_CHECK(block->alloc(total, st));
         p->b.out_q = block->q;
         p->b.out_e = block->e;
         p->b.out_tin = block->tin;
@@ -494,22 +493,23 @@ ts_status search_batch(const Index *ix, uint32_t nreq, const ts_segments *qs,
     return TS_OK;
 }
 
-ts_status RowBlock::alloc(uint64_t n)
+ts_status RowBlock::alloc(uint64_t n, cudaStream_t s)
 {
-    TS_CUDA(cudaMalloc((void **)&q, sizeof(uint32_t) * n));
-    TS_CUDA(cudaMalloc((void **)&e, sizeof(uint32_t) * n));
-    TS_CUDA(cudaMalloc((void **)&tin, sizeof(double) * n));
-    TS_CUDA(cudaMalloc((void **)&tout, sizeof(double) * n));
+    TS_CUDA(pool_malloc((void **)&q, sizeof(uint32_t) * n, s));
+    TS_CUDA(pool_malloc((void **)&e, sizeof(uint32_t) * n, s));
+    TS_CUDA(pool_malloc((void **)&tin, sizeof(double) * n, s));
+    TS_CUDA(pool_malloc((void **)&tout, sizeof(double) * n, s));
     return TS_OK;
 }
 
+// The rows are handed out only after the kernels that wrote them completed; the memory goes
+// back to the library's pool.
 RowBlock::~RowBlock()
 {
-    if (q || e || tin || tout) cudaDeviceSynchronize();
-    if (q) cudaFree(q);
-    if (e) cudaFree(e);
-    if (tin) cudaFree(tin);
-    if (tout) cudaFree(tout);
+    if (q) cudaFreeAsync(q, 0);
+    if (e) cudaFreeAsync(e, 0);
+    if (tin) cudaFreeAsync(tin, 0);
+    if (tout) cudaFreeAsync(tout, 0);
 }
 
 }  // namespace ts

@@ -56,7 +56,7 @@ struct BatchPlan {
 struct RowBlock {
     uint32_t *q = nullptr, *e = nullptr;
     double *tin = nullptr, *tout = nullptr;
-    ts_status alloc(uint64_t n);
+    ts_status alloc(uint64_t n, cudaStream_t s);
     ~RowBlock();
 };
 

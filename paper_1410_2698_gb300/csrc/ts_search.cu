@@ -624,11 +624,14 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         double tin = 0.0, tout = 0.0;
         uint32_t eid = 0;
         const uint32_t tile = tw & PK_MAX_TILES;
+        // the count pass computes hit intervals only while the scratch still has room (after
+        // an overflow the write pass sweeps and computes them)
+        const bool interval = PASS == PASS_WRITE ||
+                              (P.scap != 0 && __ldcg(&B.stats[ST_SCRATCH]) <= P.scap);
         if ((uint32_t)lane < nflush) {
             const uint32_t *ids = P.ids[tw >> 29];
             eid = ids ? ids[pos] : pos;
-            h = exact_test(B.qd + qi, P.seg + eid, PASS == PASS_WRITE || P.scap != 0, &tin,
-                           &tout);
+            h = exact_test(B.qd + qi, P.seg + eid, interval, &tin, &tout);
         }
         const unsigned hm = __ballot_sync(FULL, h);
         if (!hm) return;
@@ -645,7 +648,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 if (lane == 0) base = atomicAdd(&B.stats[ST_SCRATCH], (unsigned long long)__popc(hm));
                 base = __shfl_sync(FULL, base, 0);
                 const unsigned long long slot = base + __popc(hm & lt_mask);
-                if (h && slot < P.scap) {
+                if (h && slot < P.scap && interval) {
                     B.s_tile[slot] = tile;
                     B.s_rank[slot] = rank;
                     B.s_q[slot] = ql;

@@ -1,15 +1,19 @@
 // ts_server.cu -- the served search: a request loop on a resident index with continuous batching.
 //
 // Client threads submit requests (their query segments are copied into the request); one loop
-// thread forms batches from the queue in arrival order while a batch's request, query and row
+// thread forms batches from the queue in arrival order while a batch's request and query
 // capacities allow, and runs them on up to max_inflight batch plans, each with its own stream:
 // requests that arrive while a batch is on the device go into the next free plan, so batches
-// overlap on the device. A batch whose rows overflow is split and re-run; a lone request that
-// cannot fit ends with TS_ERR_CAPACITY. Completed requests get their own device rows (copied out
-// of the plan) and host timestamps. Every wait -- client waits and the loop's idle waits -- is
-// bounded.
+// overlap on the device. A batch runs in two phases: its plan (a CUDA graph) runs up to the count
+// pass and the row scan; the loop then allocates exactly the batch's rows from the library's
+// pool (admission by the memory the result needs) and launches the write phase into them. A
+// batch with more rows than max_batch_rows, or that outgrew a work capacity, is split and re-run;
+// a lone request that cannot fit ends with TS_ERR_CAPACITY. Completed requests share the batch's
+// row block (each result is a view of its rows) and carry host timestamps. Every wait -- client
+// waits and the loop's idle waits -- is bounded.
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -38,13 +42,18 @@ struct SrvReq {
     ts_status status = TS_OK;
     std::string error;
     SearchOut out;
+    std::shared_ptr<RowBlock> block;  // the batch's rows (out points into them)
 };
+
+enum { SLOT_IDLE = 0, SLOT_COUNT = 1, SLOT_WRITE = 2 };
 
 struct Slot {
     BatchPlan *plan = nullptr;
     cudaEvent_t done = nullptr;
     std::vector<SrvReq *> batch;
     bool busy = false;
+    int phase = SLOT_IDLE;
+    std::shared_ptr<RowBlock> block;
 };
 
 }  // namespace
@@ -74,15 +83,6 @@ struct Server {
 
 namespace {
 
-void free_out(SearchOut &o)
-{
-    if (o.q) cudaFreeAsync(o.q, 0);
-    if (o.e) cudaFreeAsync(o.e, 0);
-    if (o.tin) cudaFreeAsync(o.tin, 0);
-    if (o.tout) cudaFreeAsync(o.tout, 0);
-    o = SearchOut{};
-}
-
 void end_request(Server *s, SrvReq *r, ts_status st, const char *msg)
 {
     r->status = st;
@@ -91,64 +91,146 @@ void end_request(Server *s, SrvReq *r, ts_status st, const char *msg)
     r->done_us = s->now_us();
 }
 
-// Copy a request's rows out of the plan into its own device arrays.
-ts_status take_rows(BatchPlan *p, uint32_t r, SrvReq *q)
+// Re-queue a batch at the front, in order; the next batches take half as many requests. A lone
+// request that cannot fit ends with TS_ERR_CAPACITY. (Caller holds the lock.)
+void split_batch(Server *s, std::vector<SrvReq *> &batch, const char *why)
 {
-    uint64_t first = 0, count = 0;
-    TS_CHECK(plan_request_rows(p, r, &first, &count));
-    q->out.count = count;
-    q->out.stats.n_queries = q->n;
-    q->out.stats.n_hits = count;
-    if (!count) return TS_OK;
-    cudaStream_t st = p->stream;
-    TS_CUDA(pool_malloc((void **)&q->out.q, 4 * count, st));
-    TS_CUDA(pool_malloc((void **)&q->out.e, 4 * count, st));
-    TS_CUDA(pool_malloc((void **)&q->out.tin, 8 * count, st));
-    TS_CUDA(pool_malloc((void **)&q->out.tout, 8 * count, st));
-    TS_CUDA(cudaMemcpyAsync(q->out.q, p->b.out_q + first, 4 * count, cudaMemcpyDeviceToDevice, st));
-    TS_CUDA(cudaMemcpyAsync(q->out.e, p->b.out_e + first, 4 * count, cudaMemcpyDeviceToDevice, st));
-    TS_CUDA(cudaMemcpyAsync(q->out.tin, p->b.out_tin + first, 8 * count, cudaMemcpyDeviceToDevice, st));
-    TS_CUDA(cudaMemcpyAsync(q->out.tout, p->b.out_tout + first, 8 * count, cudaMemcpyDeviceToDevice, st));
-    return TS_OK;
+    if (batch.size() == 1) {
+        end_request(s, batch[0], TS_ERR_CAPACITY, why);
+    } else {
+        for (size_t i = batch.size(); i-- > 0;) {
+            batch[i]->state = RQ_QUEUED;
+            s->queue.push_front(batch[i]);
+        }
+        s->split_limit = std::max<size_t>(1, batch.size() / 2);
+    }
+    batch.clear();
+    s->cv_done.notify_all();
 }
 
-// Called by the loop when a slot's batch has completed on the device.
-void finish_slot(Server *s, Slot &sl)
+// The count phase of a slot's batch completed: allocate its rows and launch the write phase, or
+// end the batch (no rows, an error, or a split).
+void count_done(Server *s, Slot &sl)
 {
     ts_batch_status bs;
     ts_status st = plan_wait(sl.plan, &bs);
-    std::vector<SrvReq *> batch;
-    batch.swap(sl.batch);
-    sl.busy = false;
     if (st == TS_OK && bs.overflow) {
-        std::lock_guard<std::mutex> lk(s->mu);
-        if (batch.size() == 1) {
-            end_request(s, batch[0], TS_ERR_CAPACITY,
-                        "request exceeds the server's per-batch row or work capacity");
-        } else {
-            // re-queue at the front, in order; the next batches take half as many requests
-            for (size_t i = batch.size(); i-- > 0;) {
-                batch[i]->state = RQ_QUEUED;
-                s->queue.push_front(batch[i]);
-            }
-            s->split_limit = std::max<size_t>(1, batch.size() / 2);
+        // the batch outgrew the plan's tile or unit capacity: rebuild the plan at twice what the
+        // device reported and run the batch again, unsplit
+        BatchPlan *p = sl.plan;
+        const uint64_t T = (uint64_t)p->h_out->hdr[HDR_T_LO] |
+                           ((uint64_t)p->h_out->hdr[HDR_T_HI] << 32);
+        uint64_t units = 0;
+        if (p->b.quoff) {
+            uint32_t u = 0;
+            if (cudaMemcpy(&u, p->b.quoff + p->h_run[0], 4, cudaMemcpyDeviceToHost) == cudaSuccess)
+                units = u;
+            cudaGetLastError();
         }
-        s->cv_done.notify_all();
+        ts_batch_params bp = p->prm;
+        bool grow = false;
+        if (T > p->caps.tiles) {
+            bp.max_tiles = 2 * T;
+            grow = true;
+        }
+        if (units > p->caps.units) {
+            bp.max_units = 2 * (uint64_t)units;
+            bp.max_tiles = std::max<uint64_t>(bp.max_tiles, p->caps.tiles);
+            grow = true;
+        }
+        BatchPlan *np = nullptr;
+        if (grow && create_plan(p->ix, &bp, nullptr, false, &np) == TS_OK) {
+            destroy_plan(p);
+            sl.plan = np;
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (size_t i = sl.batch.size(); i-- > 0;) {
+                sl.batch[i]->state = RQ_QUEUED;
+                s->queue.push_front(sl.batch[i]);
+            }
+            sl.batch.clear();
+            sl.busy = false;
+            sl.phase = SLOT_IDLE;
+            return;
+        }
+    }
+    if (st == TS_OK && (bs.overflow || bs.rows > s->prm.max_batch_rows)) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        split_batch(s, sl.batch, "request exceeds the server's per-batch row or work capacity");
+        sl.busy = false;
+        sl.phase = SLOT_IDLE;
         return;
     }
-    if (st == TS_OK) {
-        for (uint32_t r = 0; r < batch.size() && st == TS_OK; r++) st = take_rows(sl.plan, r, batch[r]);
+    if (st == TS_OK && bs.rows > 0) {
+        BatchPlan *p = sl.plan;
+        auto block = std::make_shared<RowBlock>();
+        st = block->alloc(bs.rows, p->stream);
         if (st == TS_OK) {
-            cudaError_t e = cudaStreamSynchronize(sl.plan->stream);
-            if (e != cudaSuccess) st = cuda_status(e, "cudaStreamSynchronize(server)");
+            p->b.out_q = block->q;
+            p->b.out_e = block->e;
+            p->b.out_tin = block->tin;
+            p->b.out_tout = block->tout;
+            p->caps.rows = bs.rows;
+            st = pipe_write(p->ix, p->d_reqs, p->b, p->caps, p->stream);
+        }
+        if (st == TS_OK) {
+            cudaError_t e = cudaMemcpyAsync(&p->h_out->status, p->b.status, 4,
+                                            cudaMemcpyDeviceToHost, p->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(sl.done, p->stream);
+            if (e != cudaSuccess) st = cuda_status(e, "server write phase");
+        }
+        if (st == TS_OK) {
+            sl.block = block;
+            sl.phase = SLOT_WRITE;
+            return;
         }
     }
+    // no rows, or a failure: the batch ends here
     std::lock_guard<std::mutex> lk(s->mu);
     const char *msg = st == TS_OK ? nullptr : last_error();
-    for (SrvReq *q : batch) {
-        if (st != TS_OK) free_out(q->out);
+    for (SrvReq *q : sl.batch) {
+        q->out = SearchOut{};
+        q->out.stats.n_queries = q->n;
         end_request(s, q, st, msg);
     }
+    sl.batch.clear();
+    sl.busy = false;
+    sl.phase = SLOT_IDLE;
+    if (st == TS_OK) s->split_limit = 0;
+    s->cv_done.notify_all();
+}
+
+// The write phase of a slot's batch completed: every request gets a view of its rows.
+void write_done(Server *s, Slot &sl)
+{
+    BatchPlan *p = sl.plan;
+    ts_status st = TS_OK;
+    cudaError_t e = cudaEventSynchronize(sl.done);
+    if (e != cudaSuccess) st = cuda_status(e, "server write phase");
+    if (st == TS_OK && p->h_out->status) st = read_dev_status(p->h_out->status);
+    std::lock_guard<std::mutex> lk(s->mu);
+    const char *msg = st == TS_OK ? nullptr : last_error();
+    for (uint32_t r = 0; r < sl.batch.size(); r++) {
+        SrvReq *q = sl.batch[r];
+        if (st == TS_OK) {
+            const uint64_t a = p->h_row0[r], n = p->h_row0[r + 1] - a;
+            q->out = SearchOut{};
+            q->out.count = n;
+            q->out.stats.n_queries = q->n;
+            q->out.stats.n_hits = n;
+            if (n) {
+                q->out.q = sl.block->q + a;
+                q->out.e = sl.block->e + a;
+                q->out.tin = sl.block->tin + a;
+                q->out.tout = sl.block->tout + a;
+                q->block = sl.block;
+            }
+        }
+        end_request(s, q, st, msg);
+    }
+    sl.batch.clear();
+    sl.block.reset();
+    sl.busy = false;
+    sl.phase = SLOT_IDLE;
     if (st == TS_OK) s->split_limit = 0;
     s->cv_done.notify_all();
 }
@@ -192,6 +274,7 @@ ts_status launch_slot(Server *s, Slot &sl)
     }
     TS_CHECK(plan_run(sl.plan, (uint32_t)sl.batch.size(), segs.data(), qps.data(), nullptr));
     TS_CUDA(cudaEventRecord(sl.done, sl.plan->stream));
+    sl.phase = SLOT_COUNT;
     return TS_OK;
 }
 
@@ -210,7 +293,7 @@ void loop(Server *s)
             cudaError_t q = cudaEventQuery(sl.done);
             if (q == cudaErrorNotReady) continue;
             lk.unlock();
-            finish_slot(s, sl);
+            if (sl.phase == SLOT_COUNT) count_done(s, sl); else write_done(s, sl);
             lk.lock();
             progressed = true;
         }
@@ -285,11 +368,12 @@ ts_status server_create(const Index *ix, const ts_server_params *prm, Server **o
     memset(&bp, 0, sizeof(bp));
     bp.max_requests = prm->max_batch_requests;
     bp.max_queries = prm->max_batch_queries;
-    bp.max_rows = prm->max_batch_rows;
     bp.tile_records = prm->tile_records;
     bp.use_graph = prm->use_graph;
+    bp.scratch_rows = prm->scratch_rows ? prm->scratch_rows : SCRATCH_MAX;
     for (Slot &sl : s->slots) {
-        ts_status st = create_plan(ix, &bp, nullptr, true, &sl.plan);
+        // the plans run up to the row scan; every batch's rows are allocated at its exact size
+        ts_status st = create_plan(ix, &bp, nullptr, false, &sl.plan);
         if (st == TS_OK) {
             cudaError_t e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
             if (e != cudaSuccess) st = cuda_status(e, "cudaEventCreate(server)");
@@ -350,7 +434,7 @@ ts_status server_submit(Server *s, const ts_segments *q, const ts_query_params *
 }
 
 ts_status server_wait(Server *s, uint64_t ticket, uint32_t timeout_ms, SearchOut *out,
-                      ts_request_timing *timing)
+                      std::shared_ptr<RowBlock> *block, ts_request_timing *timing)
 {
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->reqs.find(ticket);
@@ -377,10 +461,10 @@ ts_status server_wait(Server *s, uint64_t ticket, uint32_t timeout_ms, SearchOut
     const ts_status st = r->status;
     if (st == TS_OK) {
         *out = r->out;
+        if (block) *block = r->block;
         r->out = SearchOut{};
     } else {
         set_error("%s", r->error.c_str());
-        free_out(r->out);
     }
     delete r;
     return st;
@@ -413,10 +497,7 @@ void server_destroy(Server *s)
         s->cv_work.notify_all();
     }
     if (s->th.joinable()) s->th.join();
-    for (auto &kv : s->reqs) {
-        free_out(kv.second->out);
-        delete kv.second;
-    }
+    for (auto &kv : s->reqs) delete kv.second;  // (undelivered rows go with their block)
     for (Slot &sl : s->slots) {
         if (sl.plan) destroy_plan(sl.plan);
         if (sl.done) cudaEventDestroy(sl.done);

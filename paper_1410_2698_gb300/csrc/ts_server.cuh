@@ -1,7 +1,9 @@
 // ts_server.cuh -- the served search (request loop with continuous batching).
 #pragma once
 
-#include "ts_search.cuh"
+#include <memory>
+
+#include "ts_batch.cuh"
 
 namespace ts {
 
@@ -13,7 +15,7 @@ ts_status server_create(const Index *ix, const ts_server_params *prm, Server **o
 ts_status server_submit(Server *s, const ts_segments *q, const ts_query_params *qp,
                         uint64_t *ticket);
 ts_status server_wait(Server *s, uint64_t ticket, uint32_t timeout_ms, SearchOut *out,
-                      ts_request_timing *timing);
+                      std::shared_ptr<RowBlock> *block, ts_request_timing *timing);
 ts_status server_cancel(Server *s, uint64_t ticket);
 void server_destroy(Server *s);
 
