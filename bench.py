@@ -81,6 +81,8 @@ def load_workload(name, rank):
         return workloads.dense()
     if name == "merger-like":
         return workloads.merger_like()
+    if name == "merger-like-2m":  # a tenth of the particles (profiling size)
+        return workloads.merger_like(n_per_cluster=5000, n_query_traj=200)
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -228,8 +228,9 @@ def merger_like(seed_offset: int = 0, n_per_cluster: int = 50000, n_samples: int
         q_ids.append(qrng.choice(core, size=min(per, core.size), replace=False))
     q_traj = np.sort(np.concatenate(q_ids))
     q = _query_from_traj(db, n_samples - 1, q_traj)
-    return Workload("merger-like-20m", db, q, 0.0, float(n_samples - 1), (1.0, 5.0),
-                    np.arange(n) * (n_samples - 1), q_traj)
+    nseg = n * (n_samples - 1)
+    return Workload(f"merger-like-{nseg // 1000000}m", db, q, 0.0, float(n_samples - 1),
+                    (1.0, 5.0), np.arange(n) * (n_samples - 1), q_traj)
 
 
 @dataclasses.dataclass
