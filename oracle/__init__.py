@@ -56,6 +56,9 @@ def _load():
             lib.orc_search.restype = _I64
             lib.orc_search_count.argtypes = [_I64, _P, _I64, _P, _D, _D, _D, _I32, _P, _P]
             lib.orc_search_count.restype = _I64
+            lib.orc_search_mt.argtypes = [_I64, _P, _I64, _P, _D, _D, _D, _I32, _P, _I32, _P, _P,
+                                          _P, _P, _P, _P]
+            lib.orc_search_mt.restype = _I64
             lib.orc_openmp_max_threads.argtypes = []
             lib.orc_openmp_max_threads.restype = _I32
             lib.orc_temporal_index.argtypes = [_I64, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P]
@@ -129,10 +132,33 @@ def eval_pairs(db, queries, qi, ei, t_start, t_end, d):
     return hit.astype(bool), tin, tout, smin
 
 
-def search(db, queries, t_start, t_end, d):
-    """All-pairs distance threshold search (Sec. 3.1) with exact temporal pruning. Returns a dict
-    of arrays q_idx, e_idx, t_in, t_out, s_min sorted by (q_idx, e_idx), and n_tests."""
+def search(db, queries, t_start, t_end, d, threads=None):
+    """All-pairs distance threshold search (Sec. 3.1) with exact temporal pruning, on `threads`
+    OpenMP threads (all by default; 1 = the single-threaded loop). Returns a dict of arrays
+    q_idx, e_idx, t_in, t_out, s_min sorted by (q_idx, e_idx), and n_tests."""
     lib = _load()
+    if threads is None:
+        threads = max_threads()
+    if threads > 1:
+        e, q = _cols(db), _cols(queries)
+        cnt = np.zeros(max(q.n, 1), dtype=np.int64)
+        ntests = np.zeros(1, dtype=np.int64)
+        total = lib.orc_search_mt(e.n, e.ptr, q.n, q.ptr, t_start, t_end, d, int(threads),
+                                  _ptr(cnt), 0, None, None, None, None, None, _ptr(ntests))
+        if total < 0:
+            raise MemoryError("oracle allocation failed")
+        oq = np.empty(total, dtype=np.uint32)
+        oe = np.empty(total, dtype=np.uint32)
+        tin, tout, smin = (np.empty(total) for _ in range(3))
+        if total:
+            got = lib.orc_search_mt(e.n, e.ptr, q.n, q.ptr, t_start, t_end, d, int(threads),
+                                    _ptr(cnt), 1, _ptr(oq), _ptr(oe), _ptr(tin), _ptr(tout),
+                                    _ptr(smin), None)
+            if got != total:
+                raise RuntimeError("oracle: the two passes disagree")
+        order = np.lexsort((oe, oq))
+        return {"q_idx": oq[order], "e_idx": oe[order], "t_in": tin[order],
+                "t_out": tout[order], "s_min": smin[order], "n_tests": int(ntests[0])}
     e, q = _cols(db), _cols(queries)
     cap = 1 << 16
     while True:

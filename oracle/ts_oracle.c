@@ -265,6 +265,87 @@ int64_t orc_search(int64_t ne, const double *const *e, int64_t nq, const double 
 }
 
 /*
+ * The same search over `nthreads` OpenMP threads: a first pass counts every query's hits into
+ * cnt[nq] (skipped when have_counts is set: cnt already holds them), and when out_q is not NULL a
+ * second pass writes every query's hits at the exclusive prefix sum of the counts, in the same
+ * (query, entry time order) order as orc_search. Returns the total hit count (-1 on allocation
+ * failure); n_tests receives the pairs evaluated by the counting pass.
+ */
+int64_t orc_search_mt(int64_t ne, const double *const *e, int64_t nq, const double *const *q,
+                      double Ts, double Te, double d, int32_t nthreads, int64_t *cnt,
+                      int32_t have_counts, uint32_t *out_q, uint32_t *out_e, double *out_tin,
+                      double *out_tout, double *out_smin, int64_t *n_tests)
+{
+    time_order o;
+    if (time_order_build(ne, e[3], e[7], &o) != 0) return -1;
+    if (nthreads < 1) nthreads = 1;
+    int64_t tests = 0;
+    if (!have_counts) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 16) reduction(+ : tests)
+#endif
+        for (int64_t i = 0; i < nq; i++) {
+            orc_seg qs;
+            seg_load(q, i, &qs);
+            cnt[i] = 0;
+            double w0 = dmax(qs.t0, Ts), w1 = dmin(qs.t1, Te);
+            if (!(w0 < w1)) continue;
+            int64_t lo = first_pmax_above(&o, w0), hi = first_t0_at_or_above(&o, w1);
+            int64_t c = 0;
+            for (int64_t p = lo; p < hi; p++) {
+                orc_seg es;
+                seg_load(e, o.perm[p], &es);
+                double tin, tout, smin;
+                tests++;
+                c += orc_pair(&qs, &es, Ts, Te, d, &tin, &tout, &smin);
+            }
+            cnt[i] = c;
+        }
+        if (n_tests) *n_tests = tests;
+    }
+    int64_t total = 0;
+    for (int64_t i = 0; i < nq; i++) total += cnt[i];
+    if (!out_q) {
+        time_order_free(&o);
+        return total;
+    }
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nq + 1));
+    if (!off) {
+        time_order_free(&o);
+        return -1;
+    }
+    off[0] = 0;
+    for (int64_t i = 0; i < nq; i++) off[i + 1] = off[i] + cnt[i];
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < nq; i++) {
+        if (!cnt[i]) continue;
+        orc_seg qs;
+        seg_load(q, i, &qs);
+        double w0 = dmax(qs.t0, Ts), w1 = dmin(qs.t1, Te);
+        int64_t lo = first_pmax_above(&o, w0), hi = first_t0_at_or_above(&o, w1);
+        int64_t k = off[i];
+        for (int64_t p = lo; p < hi; p++) {
+            orc_seg es;
+            seg_load(e, o.perm[p], &es);
+            double tin, tout, smin;
+            if (orc_pair(&qs, &es, Ts, Te, d, &tin, &tout, &smin)) {
+                out_q[k] = (uint32_t)i;
+                out_e[k] = (uint32_t)o.perm[p];
+                out_tin[k] = tin;
+                out_tout[k] = tout;
+                if (out_smin) out_smin[k] = smin;
+                k++;
+            }
+        }
+    }
+    free(off);
+    time_order_free(&o);
+    return total;
+}
+
+/*
  * The same search, counting hits only, over `nthreads` OpenMP threads (queries split among
  * threads). Used as the multithreaded CPU baseline. Returns the hit count (-1 on failure);
  * n_tests and n_qsegs (queries with a non-empty clipped window) are written when non-NULL.

@@ -51,14 +51,97 @@ def dense_small():
     return workloads.dense()
 
 
-@pytest.mark.parametrize("d", [0.5, 2.0])
-def test_dense_sampled(dense_small, d):
-    w = dense_small
-    q = _trajectory_sample(w, 6, seed=7)
-    ref = oracle.search(w.db, q, w.t_start, w.t_end, d)
-    for kind in ("temporal", "spatiotemporal", "spatial"):
-        idx = api.ts_build_index(w.db, kind=kind)
-        got = api.ts_search(idx, q, d, w.t_start, w.t_end).to_host(sort=True)
-        parity.compare(got, ref, w.db, q, w.t_start, w.t_end, d)
+@pytest.fixture(scope="module")
+def dense_indexes(dense_small):
+    out = {k: api.ts_build_index(dense_small.db, kind=k)
+           for k in ("temporal", "spatiotemporal", "spatial")}
+    yield out
+    for idx in out.values():
         idx.free()
-    assert ref["q_idx"].size > q.n  # dense: more than the self matches
+
+
+@pytest.mark.parametrize("d", [0.5, 2.0])
+def test_dense_full(dense_small, dense_indexes, d):
+    """The dense configuration in full: all 500 query trajectories against the 2M segments."""
+    w = dense_small
+    ref = oracle.search(w.db, w.queries, w.t_start, w.t_end, d)
+    for kind, idx in dense_indexes.items():
+        got = api.ts_search(idx, w.queries, d, w.t_start, w.t_end).to_host(sort=True)
+        parity.compare(got, ref, w.db, w.queries, w.t_start, w.t_end, d)
+    assert ref["q_idx"].size > w.queries.n  # dense: more than the self matches
+
+
+@pytest.fixture(scope="module")
+def merger():
+    return workloads.merger_like()
+
+
+@pytest.fixture(scope="module")
+def merger_indexes(merger):
+    out = {k: api.ts_build_index(merger.db, kind=k)
+           for k in ("temporal", "spatiotemporal", "spatial")}
+    yield out
+    for idx in out.values():
+        idx.free()
+
+
+@pytest.mark.parametrize("d", [1.0, 5.0])
+def test_merger_like_sampled(merger, merger_indexes, d):
+    """The merger-like configuration (20M segments) on a seeded 1% of its query trajectories
+    (20 of 2,000), plain searches with every index and a batch plan against the oracle."""
+    w = merger
+    q = _trajectory_sample(w, 20, seed=11)
+    ref = oracle.search(w.db, q, w.t_start, w.t_end, d)
+    first = None
+    for kind, idx in merger_indexes.items():
+        got = api.ts_search(idx, q, d, w.t_start, w.t_end).to_host(sort=True)
+        if first is None:
+            parity.compare(got, ref, w.db, q, w.t_start, w.t_end, d)
+            first = got
+        else:  # every index returns the same rows (bit for bit, sorted)
+            for key in ("q_idx", "e_idx", "t_in", "t_out"):
+                assert np.array_equal(got[key], first[key]), (kind, key)
+    plan = api.BatchPlan(merger_indexes["spatiotemporal"], max_requests=2, max_queries=2 * q.n,
+                         max_rows=2 * ref["q_idx"].size + (1 << 16), max_tiles=1 << 22)
+    half = q.take(np.arange(q.n // 2))
+    plan.run([(q, d, w.t_start, w.t_end), (half, d, w.t_start, w.t_end)])
+    st = plan.wait()
+    assert not st["overflow"]
+    batched = plan.request_to_host(0, sort=True)
+    for key in ("q_idx", "e_idx", "t_in", "t_out"):
+        assert np.array_equal(batched[key], first[key]), key
+    plan.free()
+    assert ref["q_idx"].size > 10 * q.n  # hit-dense: many neighbours per query segment
+
+
+def test_served_on_merger_like_equals_alone(merger, merger_indexes):
+    """Served requests on the resident merger-like database (small runs of core trajectories,
+    own intervals and d) equal the same requests searched alone; one against the oracle."""
+    w = merger
+    rng = np.random.default_rng(23)
+    seg_per = w.queries.n // len(w.query_traj_ids)
+    reqs = []
+    for _ in range(12):
+        k = int(rng.integers(1, 4))
+        pick = rng.choice(len(w.query_traj_ids), size=k, replace=False)
+        L = int(rng.integers(10, 40))
+        s0 = int(rng.integers(0, seg_per - L))
+        idx = (pick[:, None] * seg_per + s0 + np.arange(L)[None, :]).ravel()
+        q = w.queries.take(idx)
+        d = float(np.exp(rng.uniform(np.log(0.5), np.log(10.0))))
+        reqs.append((q, d, float(q.t0.min()), float(q.t1.max())))
+    index = merger_indexes["spatiotemporal"]
+    srv = api.Server(index, max_batch_requests=8, max_batch_queries=1 << 16,
+                     max_batch_rows=1 << 26, linger_us=500)
+    tickets = [srv.submit(q, d, ts, te) for q, d, ts, te in reqs]
+    for t, (q, d, ts, te) in zip(tickets, reqs):
+        res, tm = srv.wait(t, timeout_ms=120000)
+        got = res.to_host(sort=True)
+        alone = api.ts_search(index, q, d, ts, te).to_host(sort=True)
+        for key in ("q_idx", "e_idx", "t_in", "t_out"):
+            assert np.array_equal(got[key], alone[key]), key
+        res.free()
+    srv.close()
+    q, d, ts, te = reqs[0]
+    got = api.ts_search(index, q, d, ts, te).to_host(sort=True)
+    parity.compare(got, oracle.search(w.db, q, ts, te, d), w.db, q, ts, te, d)

@@ -81,3 +81,20 @@ def test_counting_baseline_matches_search():
         assert hits == res["q_idx"].size
         assert tests == res["n_tests"]
         assert qsegs == q.n
+
+
+def test_multithreaded_search_equals_single_threaded():
+    """The two-pass multithreaded search (counts, prefix sum, rows at offsets) returns exactly the
+    single-threaded search's rows and test count, for several thread counts."""
+    rng = np.random.default_rng(13)
+    q = random_segments(rng, 120, t_range=(0, 25))
+    e = random_segments(rng, 700, t_range=(0, 25))
+    ref = oracle.search(e, q, 2.0, 22.0, 1.8, threads=1)
+    assert ref["q_idx"].size > 50
+    for threads in (2, 5):
+        got = oracle.search(e, q, 2.0, 22.0, 1.8, threads=threads)
+        for k in ("q_idx", "e_idx", "t_in", "t_out", "s_min"):
+            np.testing.assert_array_equal(got[k], ref[k])
+        assert got["n_tests"] == ref["n_tests"]
+    empty = oracle.search(e, q, 40.0, 50.0, 1.8, threads=3)  # no window overlaps
+    assert empty["q_idx"].size == 0 and empty["n_tests"] == 0
