@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="records per work tile (0 = default)")
     ap.add_argument("--pair-blocks", type=int, default=0, help="pair kernel blocks (0 = all)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="default index parameters, tiles and pair grid instead of the "
+                         "autotuner's (which times the batched form before the timed region)")
     ap.add_argument("--serial-plans", action="store_true",
                     help="one batch plan at a time (automatic when the plans would not fit)")
     ap.add_argument("--served-index", default="spatiotemporal")
@@ -220,7 +223,16 @@ def run_gpu(args):
     torch.cuda.set_stream(torch.cuda.Stream(device=dev))
     w = load_workload(args.workload, rank)
     kinds = [k for k in args.indexes.split(",") if k]
-    indexes = {k: api.ts_build_index(w.db, kind=k) for k in kinds}
+    tuned = {}
+    if args.autotune:
+        # the autotuner times the batched form on this workload's requests (outside the timed
+        # region) and caches its choice per workload and GPU
+        from paper_1410_2698_gb300 import autotune
+        treqs = [(w.queries, d, w.t_start, w.t_end) for d in w.distances]
+        for k in kinds:
+            tuned[k] = autotune.tune(w.db, treqs, k, repeats=2)
+    indexes = {k: api.ts_build_index(w.db, kind=k, **(tuned[k]["index"] if k in tuned else {}))
+               for k in kinds}
     qdev = {f: torch.from_numpy(getattr(w.queries, f)).to(dev) for f in Segments.FIELDS}
     torch.cuda.synchronize()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
@@ -265,8 +277,10 @@ def run_gpu(args):
             max(1 << 20, 2 * rows_per_batch[k])
         return api.BatchPlan(indexes[k], max_requests=len(reqs),
                              max_queries=w.queries.n * len(reqs), max_rows=rows, use_graph=True,
-                             stream=0 if own_stream else None, tile_records=args.tile,
-                             pair_blocks=args.pair_blocks, max_units=units[k],
+                             stream=0 if own_stream else None,
+                             tile_records=tuned[k]["tile_records"] if k in tuned else args.tile,
+                             pair_blocks=tuned[k]["pair_blocks"] if k in tuned else
+                             args.pair_blocks, max_units=units[k],
                              max_tiles=tiles_per_batch[k] + tiles_per_batch[k] // 10 + 65536)
 
     batch_stats = []
@@ -418,6 +432,10 @@ def run_gpu(args):
         "breakdown": breakdown,
     }
     line["config"]["plans"] = "one at a time" if serial else "resident together, overlapped"
+    if tuned:
+        line["config"]["autotuned"] = {k: {"index": v["index"], "tile_records": v["tile_records"],
+                                           "pair_blocks": v["pair_blocks"]}
+                                       for k, v in tuned.items()}
     if not args.no_e2e:
         if serial:
             line["e2e"] = run_e2e(args, api, w, None, kinds, make_plan)

@@ -62,24 +62,43 @@ def _store(path, cache):
     os.replace(tmp, path)
 
 
-def _time_plan(index, requests, tile, pair_blocks, max_rows, repeats):
-    plan = api.BatchPlan(index, max_requests=len(requests),
-                         max_queries=sum(q.n for q, *_ in requests), max_rows=max_rows,
-                         tile_records=tile, use_graph=True, pair_blocks=pair_blocks)
-    try:
-        plan.run(requests)
-        st = plan.wait()  # warm-up (and graph capture)
-        if st["overflow"]:
-            return None, st
-        best = float("inf")
-        for _ in range(repeats):
-            t0 = time.perf_counter()
+def _units(index, requests, kind):
+    """Unit capacity of a plan: grid indexes hold one unit per z-run of a query's cells (counted
+    by the schedule); the other indexes one per query (0 = the plan's default)."""
+    if kind != "spatial":
+        return 0
+    u = sum(int(api.ts_schedule(index, q, d, ts, te)[1].sum()) for q, d, ts, te in requests)
+    return u + u // 10 + 1024
+
+
+def _time_plan(index, requests, tile, pair_blocks, max_rows, repeats, units=0):
+    """Best wall time of `repeats` runs of a plan over the requests (after a warm-up run that
+    also captures the graph). A run that outgrows the plan's rows or tiles is retried with the
+    exact counts the device reported."""
+    tiles = 0
+    st = None
+    for _ in range(3):
+        plan = api.BatchPlan(index, max_requests=len(requests),
+                             max_queries=sum(q.n for q, *_ in requests), max_rows=max_rows,
+                             tile_records=tile, use_graph=True, pair_blocks=pair_blocks,
+                             max_units=units, max_tiles=tiles)
+        try:
             plan.run(requests)
-            st = plan.wait()
-            best = min(best, time.perf_counter() - t0)
-        return best, st
-    finally:
-        plan.free()
+            st = plan.wait()  # warm-up (and graph capture)
+            if st["overflow"]:
+                max_rows = max(max_rows, st["rows"] + st["rows"] // 10 + 1024)
+                tiles = max(tiles, 2 * st["stats"]["n_tiles"] + 65536)
+                continue
+            best = float("inf")
+            for _ in range(repeats):
+                t0 = time.perf_counter()
+                plan.run(requests)
+                st = plan.wait()
+                best = min(best, time.perf_counter() - t0)
+            return best, st
+        finally:
+            plan.free()
+    return None, st
 
 
 def tune(db, requests, kind, cache_path=DEFAULT_CACHE, repeats=3, max_rows=1 << 24,
@@ -114,7 +133,8 @@ def tune(db, requests, kind, cache_path=DEFAULT_CACHE, repeats=3, max_rows=1 << 
     for params in candidates:
         idx = api.ts_build_index(db, kind=kind, **params)
         try:
-            t, st = _time_plan(idx, requests, 256, 0, max_rows, repeats)
+            t, st = _time_plan(idx, requests, 256, 0, max_rows, repeats,
+                               _units(idx, requests, kind))
         finally:
             idx.free()
         if t is None:
@@ -130,10 +150,11 @@ def tune(db, requests, kind, cache_path=DEFAULT_CACHE, repeats=3, max_rows=1 << 
         raise RuntimeError("autotune: every candidate overflowed max_rows")
     idx = api.ts_build_index(db, kind=kind, **best[0])
     tile_best = (256, 0, best[1])
+    units = _units(idx, requests, kind)
     try:
         for tile in TILES:
             for pb in (0, 152):  # all resident blocks, or one block per SM
-                t, st = _time_plan(idx, requests, tile, pb, max_rows, repeats)
+                t, st = _time_plan(idx, requests, tile, pb, max_rows, repeats, units)
                 if t is not None:
                     trials.append({"params": dict(best[0]), "tile_records": tile,
                                    "pair_blocks": pb, "s": t})
