@@ -171,6 +171,20 @@ ts_status ts_schedule(const ts_index *idx, const ts_segments *q, const ts_query_
 ts_status ts_search(const ts_index *idx, const ts_segments *q, const ts_query_params *qp,
                     void *stream, ts_result **out);
 
+/*
+ * Stationary-point search (the fixed-point queries of Sec. 1, e.g. every star that comes within d
+ * of a supernova's position while its radiation passes): every database segment within d of one
+ * of n fixed points (x[i], y[i], z[i]) at some instant of [qp->t_start, qp->t_end]. Each point is
+ * searched as a query segment that stays at its position over the whole interval (zero spatial
+ * length, a valid segment of Sec. 3.1), so the pair test and its interval are the general ones.
+ * x, y, z: n doubles each, in host memory when on_host is non-zero, else in device memory (read
+ * on `stream`). The interval must have positive length (TS_ERR_INVALID_ARG otherwise). q_idx in
+ * the result is the point's index; results, capacity and errors are as for ts_search.
+ */
+ts_status ts_search_points(const ts_index *idx, const double *x, const double *y, const double *z,
+                           uint64_t n, int32_t on_host, const ts_query_params *qp, void *stream,
+                           ts_result **out);
+
 /* Number of rows of a result. */
 uint64_t ts_result_count(const ts_result *r);
 

@@ -201,6 +201,33 @@ def ts_search(index: Index, queries, d, t_start, t_end, max_results=0, stream=No
     return Result(out, st)
 
 
+def ts_search_points(index: Index, x, y, z, d, t_start, t_end, max_results=0,
+                     stream=None) -> Result:
+    """Stationary-point search: every database segment within d of a point (x[i], y[i], z[i]) at
+    some instant of [t_start, t_end]. x, y, z: numpy arrays (host) or CUDA tensors (device)."""
+    lib = _lib.load()
+    on_host = isinstance(x, np.ndarray)
+    if on_host:
+        cols = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z)]
+        ptrs = [c.ctypes.data for c in cols]
+    else:
+        cols = [a.contiguous() for a in (x, y, z)]
+        ptrs = [c.data_ptr() for c in cols]
+    n = int(cols[0].shape[0])
+    if any(int(c.shape[0]) != n for c in cols):
+        raise ValueError("x, y and z must have the same length")
+    qp = _qparams(d, t_start, t_end, max_results)
+    out = ctypes.c_void_p()
+    st = lib.ts_search_points(index.handle, ctypes.c_void_p(ptrs[0]), ctypes.c_void_p(ptrs[1]),
+                              ctypes.c_void_p(ptrs[2]), n, int(on_host), ctypes.byref(qp),
+                              _current_stream(stream), ctypes.byref(out))
+    del cols
+    if st == 4 and out.value:
+        return Result(out, st)
+    check(st)
+    return Result(out, st)
+
+
 def ts_result_count(result: Result) -> int:
     return result.count
 

@@ -215,6 +215,30 @@ ts_status ts_search(const ts_index *h, const ts_segments *q, const ts_query_para
     });
 }
 
+ts_status ts_search_points(const ts_index *h, const double *x, const double *y, const double *z,
+                           uint64_t n, int32_t on_host, const ts_query_params *qp, void *stream,
+                           ts_result **out)
+{
+    const Index *ix = reinterpret_cast<const Index *>(h);
+    if (!ix || ix->magic != MAGIC_INDEX || !out) {
+        set_error("ts_search_points: invalid index handle or NULL out");
+        return TS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    return guarded([&]() -> ts_status {
+        ts_result *r = new ts_result();
+        r->stream = (cudaStream_t)stream;
+        ts_status st = search_points(ix, x, y, z, n, on_host != 0, qp, r->stream, &r->out);
+        if (st == TS_OK || st == TS_ERR_CAPACITY) {
+            *out = r;
+            return st == TS_OK ? clear_error(st) : st;
+        }
+        free_result_arrays(r);
+        delete r;
+        return st;
+    });
+}
+
 ts_status ts_search_batch(const ts_index *h, uint32_t nreq, const ts_segments *qs,
                           const ts_query_params *qps, void *stream, ts_result **outs)
 {

@@ -1446,6 +1446,65 @@ ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_par
     return TS_OK;
 }
 
+// The query columns of stationary points: x0 = x1 = x (likewise y, z), t0 = t_start, t1 = t_end.
+__global__ void k_point_cols(const double *x, const double *y, const double *z, uint64_t n,
+                             double ts, double te, double *cols)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const double px = x[i], py = y[i], pz = z[i];
+        cols[i] = px;
+        cols[n + i] = py;
+        cols[2 * n + i] = pz;
+        cols[3 * n + i] = ts;
+        cols[4 * n + i] = px;
+        cols[5 * n + i] = py;
+        cols[6 * n + i] = pz;
+        cols[7 * n + i] = te;
+    }
+}
+
+ts_status search_points(const Index *ix, const double *x, const double *y, const double *z,
+                        uint64_t n, bool on_host, const ts_query_params *qp, cudaStream_t s,
+                        SearchOut *out)
+{
+    TS_CHECK(check_query_params(qp));
+    if (!(qp->t_start < qp->t_end)) {
+        set_error("ts_search_points: the interval must have positive length");
+        return TS_ERR_INVALID_ARG;
+    }
+    if (n && (!x || !y || !z)) {
+        set_error("ts_search_points: NULL coordinate array");
+        return TS_ERR_INVALID_ARG;
+    }
+    *out = SearchOut{};
+    if (n == 0) return TS_OK;
+    DevBuf pts, cols;
+    const double *px = x, *py = y, *pz = z;
+    if (on_host) {
+        TS_CHECK(pts.alloc(sizeof(double) * 3 * n, s));
+        double *d = pts.as<double>();
+        TS_CUDA(cudaMemcpyAsync(d, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        TS_CUDA(cudaMemcpyAsync(d + n, y, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        TS_CUDA(cudaMemcpyAsync(d + 2 * n, z, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        px = d;
+        py = d + n;
+        pz = d + 2 * n;
+    }
+    TS_CHECK(cols.alloc(sizeof(double) * 8 * n, s));
+    k_point_cols<<<nblk(n), TPB, 0, s>>>(px, py, pz, n, qp->t_start, qp->t_end,
+                                         cols.as<double>());
+    TS_LAUNCHED();
+    ts_segments q;
+    memset(&q, 0, sizeof(q));
+    const double *c = cols.as<double>();
+    q.x0 = c; q.y0 = c + n; q.z0 = c + 2 * n; q.t0 = c + 3 * n;
+    q.x1 = c + 4 * n; q.y1 = c + 5 * n; q.z1 = c + 6 * n; q.t1 = c + 7 * n;
+    q.n = n;
+    q.on_host = 0;
+    return search_plain(ix, &q, qp, s, out);
+}
+
 ts_status schedule_only(const Index *ix, const ts_segments *q, const ts_query_params *qp,
                         cudaStream_t s, int32_t *sel, uint64_t *lo, uint64_t *hi)
 {
