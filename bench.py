@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--served-rho", type=float, default=0.9)
     ap.add_argument("--served-only", action="store_true",
                     help="only the served form (its own JSON line) on the workload's database")
+    ap.add_argument("--study", action="store_true",
+                    help="only the index-parameter study (response vs m, v, g and d) as one JSON "
+                         "line")
     return ap.parse_args()
 
 
@@ -698,10 +701,34 @@ def run_served_only(args):
     idx.free()
 
 
+def run_study(args):
+    """The index-parameter study on the workload (plain searches, device-resident queries)."""
+    import torch
+    from paper_1410_2698_gb300 import api, autotune
+    from paper_1410_2698_gb300.workloads import Segments
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    w = load_workload(args.workload, 0)
+    dev = torch.device("cuda", local)
+    qdev = {f: torch.from_numpy(getattr(w.queries, f)).to(dev) for f in Segments.FIELDS}
+    kinds = [k for k in args.indexes.split(",") if k]
+    clocks = ClockSampler(local)
+    clocks.start()
+    rows = autotune.study(w.db, qdev, w.distances, w.t_start, w.t_end, kinds=kinds)
+    clk = clocks.stop()
+    print(json.dumps({"study": "index granularity", "workload": f"{w.name}: {w.db.n} db segments, "
+                      f"{w.queries.n} query segments", "clocks": clk, "records": rows}),
+          flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.study:
+        run_study(args)
     elif args.served_only:
         run_served_only(args)
     else:

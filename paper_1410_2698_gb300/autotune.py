@@ -167,3 +167,48 @@ def tune(db, requests, kind, cache_path=DEFAULT_CACHE, repeats=3, max_rows=1 << 
     cache[key] = out
     _store(cache_path, cache)
     return out
+
+
+STUDY = {
+    "temporal": ("t_bins", [0.25, 0.5, 1, 2, 4, 8, 16]),     # multiples of span / longest duration
+    "spatiotemporal": ("sub_bins", [1, 2, 4, 8, 16, 32, 64]),
+    "spatial": ("grid_cells", [5, 10, 25, 50, 100, 200]),
+}
+
+
+def study(db, queries, distances, t_start, t_end, kinds=("temporal", "spatiotemporal", "spatial"),
+          repeats=3):
+    """Response of the search to the index's bin granularity (the temporal bins m, the subbins v,
+    the grid cells g) at every distance: one record per (kind, value, d) with the plain search's
+    wall time (median of `repeats`), its count-pass time, the candidate tests, FP64 tests and hits,
+    and for subbins the fraction of query segments served by a subbin."""
+    span = float(db.t1.max() - db.t0.min())
+    longest = float((db.t1 - db.t0).max())
+    base = max(1.0, span / max(longest, 1e-300))
+    out = []
+    for kind in kinds:
+        name, values = STUDY[kind]
+        for v in values:
+            param = int(max(1, min(db.n, round(v * base)))) if name == "t_bins" else int(v)
+            idx = api.ts_build_index(db, kind=kind, **{name: param})
+            try:
+                for d in distances:
+                    times = []
+                    st = None
+                    for _ in range(repeats + 1):
+                        t0 = time.perf_counter()
+                        r = api.ts_search(idx, queries, d, t_start, t_end)
+                        times.append(time.perf_counter() - t0)
+                        st = r.stats
+                        r.free()
+                    times = sorted(times[1:])
+                    nq = max(st["n_qsegs"], 1)
+                    out.append({"kind": kind, name: param, "d": d,
+                                "ms": 1e3 * times[len(times) // 2],
+                                "count_pass_ms": st["ms_count_pass"], "tests": st["n_tests"],
+                                "exact": st["n_exact"], "hits": st["n_hits"],
+                                "subbin_fraction": st["n_subbin"] / nq
+                                if kind == "spatiotemporal" else None})
+            finally:
+                idx.free()
+    return out
