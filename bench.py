@@ -157,26 +157,41 @@ def measured_peaks():
         return {}
 
 
-def roofline(tot, pair_ms):
+def roofline(tot, pair_ms, peaks=None):
     """Roofline of the pair kernel (count + write passes): the slower of the FP32 filter and the
-    FP64 exact test at their pipes' peaks; algorithmic work counted once."""
+    FP64 exact test at their pipes' peaks (measured on this GPU when `peaks` is given, else
+    derived / nominal); algorithmic work counted once. Beside it, for context, the per-candidate
+    FP64 roofline (every candidate charged a full FP64 test and its 68 bytes), which the FP32
+    filter lets the kernel exceed."""
     t_s = pair_ms / 1e3
+    p32 = peaks["fp32_tflops"] if peaks else FP32_PEAK_TFLOPS
+    p64 = peaks["fp64_tflops"] if peaks else FP64_PEAK_TFLOPS
     f32 = tot["n_tests"] * PREFILTER_FLOPS
     f64 = tot["n_exact"] * EXACT_FLOPS + tot["n_hits"] * INTERVAL_FLOPS
-    lb32 = f32 / (FP32_PEAK_TFLOPS * 1e12)
-    lb64 = f64 / (FP64_PEAK_TFLOPS * 1e12)
+    lb32 = f32 / (p32 * 1e12)
+    lb64 = f64 / (p64 * 1e12)
     if lb32 >= lb64:
         ach = f32 / t_s / 1e12 if t_s > 0 else 0.0
-        peak = FP32_PEAK_TFLOPS
+        peak = p32
         pipe = "fp32 (conservative filter)"
     else:
         ach = f64 / t_s / 1e12 if t_s > 0 else 0.0
-        peak = FP64_PEAK_TFLOPS
+        peak = p64
         pipe = "fp64 (exact test)"
+    hbm = measured_peaks().get("hbm_gbs")
+    tests_s = tot["n_tests"] / t_s if t_s > 0 else 0.0
+    bound = min(p64 * 1e12 / 50.0, (hbm or 6771.1) * 1e9 / 68.0)
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak if peak else None, "traffic": None,
             "kernel": "k_pair (count + write passes)", "pipe": pipe,
-            "peak_source": "derived: 152 SMs x lanes x 2.07 GHz (FP32), GB300 nominal (FP64)"}
+            "peak_source": ("measured on this GPU: FMA loops (ts_measure_alu_peaks), "
+                            f"FP32 {p32:.1f}, FP64 {p64:.3f} TFLOP/s") if peaks else
+                           "derived: 152 SMs x lanes x 2.07 GHz (FP32), GB300 nominal (FP64)",
+            "per_candidate_fp64_roofline": {
+                "tests_per_s": tests_s, "bound_tests_per_s": bound,
+                "ratio": tests_s / bound if bound else None,
+                "note": "every candidate charged 50 FP64 flops and 68 B; the FP32 filter decides "
+                        "almost all candidates without the FP64 pipe"}}
 
 
 def _timed(args, stream, flush, step, steps=None):
@@ -238,6 +253,7 @@ def run_gpu(args):
                for k in kinds}
     qdev = {f: torch.from_numpy(getattr(w.queries, f)).to(dev) for f in Segments.FIELDS}
     torch.cuda.synchronize()
+    peaks = api.ts_measure_alu_peaks()  # roofline denominators, measured before the timed region
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
     stream = torch.cuda.current_stream()
 
@@ -400,13 +416,13 @@ def run_gpu(args):
     # roofline of the dominant kernel (the batched pair kernel, count + write passes, timed by
     # CUDA events the plan records around the passes on its stream, one plan at a time)
     if apair_ms > 0:
-        roof = roofline(atot, apair_ms)
+        roof = roofline(atot, apair_ms, peaks)
         roof["timed_form"] = "batched, one plan at a time (separate loop of the same plans)"
         roof["pair_kernel_share"] = apair_ms / sum(alone_ms) if alone_ms else None
         roof["ms_per_step_one_at_a_time"] = sum(alone_ms) / n_alone
         roof["per_index"] = per_index
     else:
-        roof = roofline(tot, pair_ms)
+        roof = roofline(tot, pair_ms, peaks)
         roof["timed_form"] = "plain"
     # whole-job aggregates (every rank processes the same amount of work)
     value = btot["n_qsegs"] * world / (batch_total / 1e3)

@@ -361,6 +361,12 @@ ts_status ts_search_brute_noalloc(const ts_segments *db, const ts_segments *q,
  * devices); the difference across a region counts the launches inside it. */
 uint64_t ts_kernel_launches(void);
 
+/* Measured arithmetic peaks of the current device, in TFLOP/s (an FMA counts two flops): FP32
+ * and FP64 fused multiply-add loops over every SM, timed with CUDA events (best of 3 after a
+ * warm-up; ~0.3 s in total). These are the denominators of the pair kernel's roofline (its filter
+ * runs on the FP32 pipe, its exact test on the FP64 pipe); the paper has no counterpart. */
+ts_status ts_measure_alu_peaks(double *fp32_tflops, double *fp64_tflops);
+
 /* Library version string. */
 const char *ts_version(void);
 

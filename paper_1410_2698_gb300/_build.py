@@ -20,7 +20,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libts_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["ts_prims.cu", "ts_index.cu", "ts_search.cu", "ts_batch.cu", "ts_server.cu",
-           "ts_api.cu", "ts_noalloc.cu"]
+           "ts_api.cu", "ts_noalloc.cu", "ts_peaks.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -114,6 +114,7 @@ SIGNATURES = {
                          _P, _P, _P]),
     "ts_search": (_S, [_P, ctypes.POINTER(ts_segments), ctypes.POINTER(ts_query_params), _P,
                        ctypes.POINTER(_P)]),
+    "ts_measure_alu_peaks": (_S, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "ts_search_points": (_S, [_P, _P, _P, _P, ctypes.c_uint64, ctypes.c_int32,
                               ctypes.POINTER(ts_query_params), _P, ctypes.POINTER(_P)]),
     "ts_result_count": (ctypes.c_uint64, [_P]),

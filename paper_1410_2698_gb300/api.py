@@ -296,6 +296,14 @@ def ts_search_brute_noalloc(db, queries, d, t_start, t_end, q_idx, e_idx, t_in, 
     return st, int(count.value)
 
 
+def ts_measure_alu_peaks() -> dict:
+    """Measured FP32 and FP64 FMA throughput of the current device (TFLOP/s)."""
+    lib = _lib.load()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(lib.ts_measure_alu_peaks(ctypes.byref(a), ctypes.byref(b)))
+    return {"fp32_tflops": a.value, "fp64_tflops": b.value}
+
+
 def ts_kernel_launches() -> int:
     return int(_lib.load().ts_kernel_launches())
 

@@ -72,6 +72,18 @@ const char *ts_version(void) { return "ts_gb300 0.1 (sm_103a)"; }
 
 const char *ts_last_error(void) { return ts::last_error(); }
 
+ts_status ts_measure_alu_peaks(double *fp32_tflops, double *fp64_tflops)
+{
+    if (!fp32_tflops || !fp64_tflops) {
+        set_error("ts_measure_alu_peaks: NULL argument");
+        return TS_ERR_INVALID_ARG;
+    }
+    return guarded([&]() -> ts_status {
+        ts_status st = measure_alu_peaks(fp32_tflops, fp64_tflops);
+        return st == TS_OK ? clear_error(st) : st;
+    });
+}
+
 uint64_t ts_kernel_launches(void) { return (uint64_t)ts::launch_count(); }
 
 ts_status ts_search_brute_noalloc(const ts_segments *db, const ts_segments *q,

@@ -108,6 +108,7 @@ unsigned long long launch_count();
 // Plain search (R = 1) with exact-size allocations; synchronises the stream.
 ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_params *qp,
                        cudaStream_t s, SearchOut *out);
+ts_status measure_alu_peaks(double *fp32_tflops, double *fp64_tflops);
 ts_status search_points(const Index *ix, const double *x, const double *y, const double *z,
                         uint64_t n, bool on_host, const ts_query_params *qp, cudaStream_t s,
                         SearchOut *out);

@@ -286,3 +286,11 @@ def test_grid_index_and_schedule_match_oracle(tiny, g):
     np.testing.assert_array_equal(ghi, cand)
     res = api.ts_search(idx, q, d, Ts, Te)
     assert res.stats["n_tests"] == int(cand.sum())  # one cell per entry: no duplicate candidates
+
+
+def test_measured_alu_peaks_are_plausible():
+    """The roofline denominators measured on the device: FP32 FMA well above FP64 FMA, both
+    within the range a GPU of this class can reach."""
+    p = api.ts_measure_alu_peaks()
+    assert 10.0 < p["fp32_tflops"] < 400.0
+    assert 0.05 < p["fp64_tflops"] < p["fp32_tflops"]
