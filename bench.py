@@ -291,22 +291,48 @@ def run_gpu(args):
         else:
             units[k] = 0  # one unit per query (the plan's default)
 
-    def make_plan(k, own_stream):
+    def make_plan(k, own_stream, pair_blocks=None):
         rows = (rows_per_batch[k] + rows_per_batch[k] // 20 + (1 << 20)) if serial else \
             max(1 << 20, 2 * rows_per_batch[k])
+        if pair_blocks is None:
+            pair_blocks = tuned[k]["pair_blocks"] if k in tuned else args.pair_blocks
         return api.BatchPlan(indexes[k], max_requests=len(reqs),
                              max_queries=w.queries.n * len(reqs), max_rows=rows, use_graph=True,
                              stream=0 if own_stream else None,
                              tile_records=tuned[k]["tile_records"] if k in tuned else args.tile,
-                             pair_blocks=tuned[k]["pair_blocks"] if k in tuned else
-                             args.pair_blocks, max_units=units[k],
+                             pair_blocks=pair_blocks, max_units=units[k],
                              max_tiles=tiles_per_batch[k] + tiles_per_batch[k] // 10 + 65536)
 
     batch_stats = []
     alone = []
     plans = {}
+    step_pair_blocks = None
+    if not serial and args.autotune and not args.pair_blocks:
+        # the plans of a step overlap on their own streams, and a persistent pair kernel holds
+        # the SMs it runs on: the pair grid is tuned on the overlapped step itself (all resident
+        # blocks, 1.5 or 1 block per SM), outside the timed region
+        best = None
+        for pb in (0, 228, 152):
+            trial = {k: make_plan(k, True, pb) for k in kinds}
+            for _ in range(8):  # warm-up (graph capture), then the timed trials
+                for k in kinds:
+                    trial[k].run(reqs, stream=0)
+                for k in kinds:
+                    trial[k].wait()
+            t0 = time.perf_counter()
+            for _ in range(20):
+                for k in kinds:
+                    trial[k].run(reqs, stream=0)
+                for k in kinds:
+                    trial[k].wait()
+            dt = time.perf_counter() - t0
+            for pl in trial.values():
+                pl.free()
+            if best is None or dt < best[1]:
+                best = (pb, dt)
+        step_pair_blocks = best[0]
     if not serial:
-        plans = {k: make_plan(k, True) for k in kinds}
+        plans = {k: make_plan(k, True, step_pair_blocks) for k in kinds}
 
         def batched_step(collect=None):
             for k in kinds:
@@ -453,7 +479,8 @@ def run_gpu(args):
     line["config"]["plans"] = "one at a time" if serial else "resident together, overlapped"
     if tuned:
         line["config"]["autotuned"] = {k: {"index": v["index"], "tile_records": v["tile_records"],
-                                           "pair_blocks": v["pair_blocks"]}
+                                           "pair_blocks": v["pair_blocks"]
+                                           if step_pair_blocks is None else step_pair_blocks}
                                        for k, v in tuned.items()}
     if not args.no_e2e:
         if serial:

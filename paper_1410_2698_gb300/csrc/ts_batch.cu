@@ -104,6 +104,7 @@ static void layout(BatchPlan *p, Carver &c)
     b.g_count = c.take<uint32_t>(k.groups);
     b.g_nseg = c.take<uint32_t>(k.groups);
     b.gmem = c.take<MemberRec>(GROUP * k.groups);
+    b.ghdr = c.take<float4>(k.groups);
     b.seg_lo = c.take<uint32_t>(GROUP * k.groups);
     b.seg_hi = c.take<uint32_t>(GROUP * k.groups);
     b.seg_sel = c.take<uint32_t>(GROUP * k.groups);
@@ -307,7 +308,7 @@ static ts_status enqueue_run(BatchPlan *p, cudaStream_t s, bool write)
         TS_CHECK(scan_u32(b.qnu, b.quoff, k.nq, b.status, s, p->d_run));
         TS_CHECK(pipe_grid_units(p->ix, k.nq, b, k, s));
     }
-    TS_CHECK(pipe_group(p->ix, k.nreq, b, k, s));
+    TS_CHECK(pipe_group(p->ix, p->d_reqs, k.nreq, b, k, s));
     TS_CUDA(record_ev(p->ev[0], s));
     TS_CHECK(pipe_count(p->ix, p->d_reqs, b, k, s));
     TS_CUDA(record_ev(p->ev[1], s));

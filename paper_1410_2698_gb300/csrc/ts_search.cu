@@ -115,16 +115,6 @@ __device__ __forceinline__ int last_start_below_t(const double *bs, uint32_t m, 
     return j;
 }
 
-// last bin with start < w1, or -1
-__device__ __forceinline__ int last_start_below(const double *bs, uint32_t m, double w1)
-{
-    uint32_t lo = 0, hi = m;
-    while (lo < hi) {
-        uint32_t mid = lo + (hi - lo) / 2;
-        if (bs[mid] >= w1) hi = mid; else lo = mid + 1;
-    }
-    return (int)lo - 1;
-}
 
 // ---------------------------------------------------------------------------------------------
 // query preparation (one thread per query segment of the batch)
@@ -301,39 +291,46 @@ __global__ void k_qprep(PrepParams P)
 
 // Grid index: one unit per (cx, cy) of a query's cell box, covering cells cz_a..cz_b (a z-run
 // of the row-major cell order, contiguous in the lookup array).
+// One warp per query segment, the lanes over the (cx, cy) columns of its cell box (row-major: the
+// unit of column c is quoff[i] + c), so the two offset loads of every column run in parallel.
 __global__ void k_grid_units(uint64_t nqcap, uint64_t ucap, KeyFmt kf, uint32_t g,
                              const uint32_t *g_off, PipeBufs b)
 {
+    const unsigned FULL = 0xffffffffu;
     const uint64_t nq = b.run ? min((uint64_t)b.run[0], nqcap) : nqcap;
     if (blockIdx.x == 0 && threadIdx.x == 0)
         b.hdr[HDR_NU] = (uint32_t)min((uint64_t)b.quoff[nq], ucap);  // unit slots of the runs
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
-         i += (uint64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nq; i += warps) {
         const uint32_t nu = b.qnu[i];
         if (!nu) continue;
-        if ((uint64_t)b.quoff[i] + nu > ucap) {  // more runs than the unit buffers hold
-            atomicOr(b.status, DEV_ERR_OVERFLOW);
+        const uint32_t u0 = b.quoff[i];
+        if ((uint64_t)u0 + nu > ucap) {  // more runs than the unit buffers hold
+            if (lane == 0) atomicOr(b.status, DEV_ERR_OVERFLOW);
             continue;
         }
         const uint32_t r = b.qreq[i];
         const uint32_t w0 = b.qcell[2 * i], w1 = b.qcell[2 * i + 1];
         const uint32_t ax = w0 & 1023u, ay = (w0 >> 10) & 1023u, az = (w0 >> 20) & 1023u;
-        const uint32_t bx = w1 & 1023u, by = (w1 >> 10) & 1023u, bz = (w1 >> 20) & 1023u;
-        uint32_t u = b.quoff[i];
+        const uint32_t by = (w1 >> 10) & 1023u, bz = (w1 >> 20) & 1023u;
+        const uint32_t ny = by - ay + 1;
         uint32_t nvalid = 0;
-        for (uint32_t cx = ax; cx <= bx; cx++)
-            for (uint32_t cy = ay; cy <= by; cy++, u++) {
-                const uint64_t row = ((uint64_t)cx * g + cy) * g;
-                const uint32_t lo = g_off[row + az], hi = g_off[row + bz + 1];
-                b.u_q[u] = (uint32_t)i;
-                b.u_lo[u] = lo;
-                b.u_hi[u] = hi;
-                b.u_sel[u] = SEL_GRID;
-                b.keys[u] = hi > lo ? unit_key(r, SEL_GRID, lo, kf) : ~0ull;
-                b.vals[u] = u;
-                nvalid += hi > lo;
-            }
-        if (nvalid) atomicAdd(&b.req_units[r], nvalid);
+        for (uint32_t c = lane; c < nu; c += 32) {
+            const uint32_t cx = ax + c / ny, cy = ay + c % ny;
+            const uint32_t u = u0 + c;
+            const uint64_t row = ((uint64_t)cx * g + cy) * g;
+            const uint32_t lo = g_off[row + az], hi = g_off[row + bz + 1];
+            b.u_q[u] = (uint32_t)i;
+            b.u_lo[u] = lo;
+            b.u_hi[u] = hi;
+            b.u_sel[u] = SEL_GRID;
+            b.keys[u] = hi > lo ? unit_key(r, SEL_GRID, lo, kf) : ~0ull;
+            b.vals[u] = u;
+            nvalid += hi > lo;
+        }
+        for (int o = 16; o; o >>= 1) nvalid += __shfl_xor_sync(FULL, nvalid, o);
+        if (lane == 0 && nvalid) atomicAdd(&b.req_units[r], nvalid);
     }
 }
 
@@ -366,7 +363,7 @@ __global__ void k_req_scan(uint32_t nreq_cap, PipeBufs b)
 // segments (a member opens a segment when its start lies beyond every earlier range of its
 // array); each segment is cut into tiles of `tile` records.
 __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, uint32_t align_sels,
-                         PipeBufs b)
+                         const ReqDesc *reqs, PipeBufs b)
 {
     // (also writes the members' records, in the group's order, for the pair kernel)
     const unsigned FULL = 0xffffffffu;
@@ -392,6 +389,8 @@ __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, uint32
         if (lane == 0) {
             b.g_first[g] = first;
             b.g_count[g] = n;
+            const ReqDesc &R = reqs[r];
+            b.ghdr[g] = make_float4(R.d_dn, R.d2u, __uint_as_float(R.q_first), 0.0f);
         }
         // key = (array, start); lanes past the group's members hold the largest key
         uint64_t key = ~0ull;
@@ -520,6 +519,8 @@ __global__ void k_tile_desc(uint64_t gcap, uint64_t tcap, uint32_t tile, PipeBuf
 struct __align__(16) WarpSmem {
     RecF stage[2][PK_CH];
     MemberRec mem[GROUP];  // the tile's group members
+    float4 ghdr;           // their request's d_dn, d2u, q_first
+    uint4 dnext;           // the next tile's descriptor (asynchronous copy during the sweep)
     RecF cbox[32];         // bounding records of the tile's chunks (arrays that have them)
     // exact-test queue, first in first out, carried from tile to tile: query index in the batch,
     // entry position in its sorted array, tile | sel << 29, query index within its request
@@ -690,7 +691,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             continue;
         }
         const uint32_t g = D.x, s0 = D.y, s1 = D.z;
-        const uint32_t sel = D.w & 7u, count = ((D.w >> 3) & 31u) + 1u, req = D.w >> 8;
+        const uint32_t sel = D.w & 7u, count = ((D.w >> 3) & 31u) + 1u;
         const uint32_t tw = (uint32_t)t | (sel << 29);
         const RecF *recs = P.rec[sel];
         const RecF *bx = P.box[sel];
@@ -701,7 +702,8 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         if (lane == 0) {
             const uint32_t mb = count * (uint32_t)sizeof(MemberRec);
             const uint32_t cb = bx ? nch * (uint32_t)sizeof(RecF) : 0u;
-            mbar_arrive_tx(&W.mbar, mb + cb);
+            mbar_arrive_tx(&W.mbar, mb + cb + (uint32_t)sizeof(float4));
+            bulk_g2s(&W.ghdr, B.ghdr + g, (uint32_t)sizeof(float4), &W.mbar);
             bulk_g2s(&W.mem[0], B.gmem + (uint64_t)g * GROUP, mb, &W.mbar);
             if (bx) bulk_g2s(&W.cbox[0], bx + s0 / PK_CH, cb, &W.mbar);
             for (uint32_t c = 0; c < 2 && c < nch; c++) {
@@ -713,19 +715,23 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         mpending = true;
         pending[0] = nch > 0;
         pending[1] = nch > 1;
-        // a group's members belong to one request: its d bounds for the gap filter
-        const ReqDesc &RQ = P.reqs[req];
-        const float d_dn = RQ.d_dn, d2u = RQ.d2u;
-        const uint32_t q_first = RQ.q_first;
         if (!mbar_wait_bounded(&W.mbar, mparity)) {
             abort = true;
             break;
         }
         mparity ^= 1u;
         mpending = false;
-        // the next tile's descriptor is in flight during the sweep
-        uint4 Dn = make_uint4(0u, 0u, 0u, 0u);
-        if (lane == 0 && t_next < ntiles) Dn = B.tdesc[t_next];
+        // a group's members belong to one request: its d bounds for the gap filter
+        const float4 GH = W.ghdr;
+        const float d_dn = GH.x, d2u = GH.y;
+        const uint32_t q_first = __float_as_uint(GH.z);
+        // the next tile's descriptor is copied into shared memory during the sweep
+        if (lane == 0 && t_next < ntiles) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(&W.dnext)),
+                         "l"(B.tdesc + t_next)
+                         : "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
 
         // members of the group: one per lane, their expanded boxes and ranges in registers
         uint32_t lo = 0, hi = 0, myq = 0;
@@ -878,12 +884,11 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 pending[st] = true;
             }
         }
+        if (lane == 0) asm volatile("cp.async.wait_all;" ::: "memory");
         __syncwarp();
         t = __shfl_sync(FULL, t_next, 0);
-        D.x = __shfl_sync(FULL, Dn.x, 0);
-        D.y = __shfl_sync(FULL, Dn.y, 0);
-        D.z = __shfl_sync(FULL, Dn.z, 0);
-        D.w = __shfl_sync(FULL, Dn.w, 0);
+        D = W.dnext;
+        __syncwarp();  // (read by every lane before the next copy)
     }
     if (!abort && qn) {
         __syncwarp();
@@ -1111,12 +1116,14 @@ ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const
 {
     (void)c;
     if (!nq) return TS_OK;
-    k_grid_units<<<nblk(nq), TPB, 0, s>>>(nq, c.units, key_fmt(ix), ix->g, ix->g_off, b);
+    const unsigned ublk = (unsigned)std::min<uint64_t>((nq * 32 + TPB - 1) / TPB, 152 * 16);
+    k_grid_units<<<ublk, TPB, 0, s>>>(nq, c.units, key_fmt(ix), ix->g, ix->g_off, b);
     TS_LAUNCHED();
     return TS_OK;
 }
 
-ts_status pipe_group(const Index *ix, uint32_t nreq, const PipeBufs &b, const PipeCaps &c,
+ts_status pipe_group(const Index *ix, const ReqDesc *reqs, uint32_t nreq, const PipeBufs &b,
+                     const PipeCaps &c,
                      cudaStream_t s)
 {
     // one bit above the key fields: a unit without candidates has key ~0 and sorts last
@@ -1126,7 +1133,8 @@ ts_status pipe_group(const Index *ix, uint32_t nreq, const PipeBufs &b, const Pi
     k_req_scan<<<1, 32, 0, s>>>(nreq, b);
     TS_LAUNCHED();
     const unsigned gblk = (unsigned)std::min<uint64_t>((c.groups * 32 + TPB - 1) / TPB, 152 * 16);
-    k_groups<<<gblk, TPB, 0, s>>>(nreq, c.groups, c.tile, ix->tbox ? (1u << SEL_T) : 0u, b);
+    k_groups<<<gblk, TPB, 0, s>>>(nreq, c.groups, c.tile, ix->tbox ? (1u << SEL_T) : 0u, reqs,
+                                  b);
     TS_LAUNCHED();
     TS_CHECK(scan_u32_to_u64(b.ntiles, b.tile_base, c.groups, s, b.hdr + HDR_G));
     k_hdr<<<1, 1, 0, s>>>(c.groups, c.tiles, b);
@@ -1318,8 +1326,9 @@ ts_status plain_prepare(const Index *ix, const double *const cols[8], uint64_t n
     if (!group) return TS_OK;
     c.groups = (units + GROUP - 1) / GROUP + 1;
     TS_CHECK(w.groups.alloc(sizeof(uint32_t) * 3 * c.groups, s));
-    TS_CHECK(w.gmem.alloc(sizeof(MemberRec) * GROUP * c.groups, s));
+    TS_CHECK(w.gmem.alloc((sizeof(MemberRec) * GROUP + sizeof(float4)) * c.groups, s));
     b.gmem = w.gmem.as<MemberRec>();
+    b.ghdr = reinterpret_cast<float4 *>(b.gmem + GROUP * c.groups);
     TS_CHECK(w.segs.alloc(sizeof(uint32_t) * 4 * GROUP * c.groups, s));
     TS_CHECK(w.ntiles.alloc(sizeof(uint32_t) * c.groups, s));
     TS_CHECK(w.tile_base.alloc(sizeof(uint64_t) * (c.groups + 1), s));
@@ -1333,7 +1342,7 @@ ts_status plain_prepare(const Index *ix, const double *const cols[8], uint64_t n
     b.ntiles = w.ntiles.as<uint32_t>();
     b.tile_base = w.tile_base.as<uint64_t>();
     c.tiles = ~0ull;  // sized after the grouping; no overflow check in the header kernel
-    TS_CHECK(pipe_group(ix, 1, b, c, s));
+    TS_CHECK(pipe_group(ix, w.reqdesc.as<ReqDesc>(), 1, b, c, s));
     return TS_OK;
 }
 

@@ -65,6 +65,7 @@ struct PipeBufs {
     // groups
     uint32_t *g_first, *g_count, *g_nseg;
     MemberRec *gmem;      // GROUP per group, in the group's (array, start) order
+    float4 *ghdr;         // per group: its request's d_dn, d2u, q_first (bits), 0
     uint32_t *seg_lo, *seg_hi, *seg_sel, *seg_t0;  // GROUP per group
     uint32_t *ntiles;
     uint64_t *tile_base;  // groups + 1
@@ -121,7 +122,8 @@ ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq
                        cudaStream_t s);
 ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const PipeCaps &c,
                           cudaStream_t s);
-ts_status pipe_group(const Index *ix, uint32_t nreq, const PipeBufs &b, const PipeCaps &c,
+ts_status pipe_group(const Index *ix, const ReqDesc *reqs, uint32_t nreq, const PipeBufs &b,
+                     const PipeCaps &c,
                      cudaStream_t s);
 ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,
                      cudaStream_t s);
