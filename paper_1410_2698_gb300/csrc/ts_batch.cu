@@ -32,25 +32,35 @@ __device__ __forceinline__ uint32_t req_of_b(const ReqDesc *reqs, uint32_t nreq,
     return lo;
 }
 
-// Copy every request's query columns into the batch's concatenated columns (8 x nq_cap).
-__global__ void k_gather_queries(const ReqDesc *reqs, const uint32_t *run, uint32_t nreq_cap,
-                                 uint64_t nq_cap, double *cat)
+static_assert(sizeof(ReqDesc) % 4 == 0, "the request table is copied as 32-bit words");
+
+// Start of a run: the request table and the run header come from the plan's mapped pinned
+// memory (written by the host before the launch), and the run's counters are reset.
+__global__ void k_run_start(const ReqDesc *h_reqs, const uint32_t *h_run, ReqDesc *d_reqs,
+                            uint32_t *d_run, uint32_t nreq_cap, PipeBufs b)
 {
-    const uint32_t nreq = min(run[1], nreq_cap);
-    const uint64_t nq = min((uint64_t)run[0], nq_cap);
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = req_of_b(reqs, nreq, i);
-        const uint64_t local = i - reqs[r].q_first;
-#pragma unroll
-        for (int k = 0; k < 8; k++) cat[(uint64_t)k * nq_cap + i] = reqs[r].cols[k][local];
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t words = (uint64_t)nreq_cap * (sizeof(ReqDesc) / 4);
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(h_reqs);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(d_reqs);
+    for (uint64_t i = tid; i < words; i += nth) dst[i] = src[i];
+    for (uint64_t i = tid; i < nreq_cap; i += nth) b.req_units[i] = 0;
+    if (tid < 4) d_run[tid] = h_run[tid];
+    if (tid < ST_NSLOTS) b.stats[tid] = 0;
+    if (tid == 0) {
+        b.status[0] = 0;
+        b.counters[0] = 0;
+        b.counters[1] = 0;
     }
 }
 
 // Row range of every request: its rows start at the offset of its first tile (groups of a
 // request are contiguous, and so are their tiles and rows).
+// (also the run's outcome -- header, statistics, status -- into the plan's mapped pinned memory,
+// where the host reads it after the stream synchronised)
 __global__ void k_req_rows(const uint32_t *run, uint32_t nreq_cap, uint64_t tcap, PipeBufs b,
-                           unsigned long long *row0)
+                           unsigned long long *row0, BatchOut *out)
 {
     const uint32_t nreq = min(run[1], nreq_cap);
     const uint64_t T = (uint64_t)b.hdr[HDR_T_LO] | ((uint64_t)b.hdr[HDR_T_HI] << 32);
@@ -59,6 +69,9 @@ __global__ void k_req_rows(const uint32_t *run, uint32_t nreq_cap, uint64_t tcap
         const uint64_t t0 = b.tile_base[b.gstart[r]];
         row0[r] = ok ? b.tile_off[t0 < T ? t0 : T] : 0ull;
     }
+    if (threadIdx.x < 8) out->hdr[threadIdx.x] = b.hdr[threadIdx.x];
+    if (threadIdx.x < ST_NSLOTS) out->stats[threadIdx.x] = b.stats[threadIdx.x];
+    if (threadIdx.x == 0) out->status = b.status[0];
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -133,8 +146,6 @@ static void layout(BatchPlan *p, Carver &c)
     p->d_reqs = c.take<ReqDesc>(k.nreq);
     p->d_run = c.take<uint32_t>(4);
     b.run = p->d_run;
-    p->d_cat = c.take<double>(8 * k.nq);
-    p->d_row0 = c.take<unsigned long long>(k.nreq + 1);
 }
 
 void destroy_plan(BatchPlan *p)
@@ -209,6 +220,18 @@ ts_status create_plan(const Index *ix, const ts_batch_params *prm, cudaStream_t 
     p->h_row0 = reinterpret_cast<unsigned long long *>(h + h_reqs + h_run + h_stage +
                                                        align256(sizeof(BatchOut)));
     memset(p->hmem, 0, p->hbytes);
+    // device views of the mapped pinned memory (the run's first and last kernels use them)
+    {
+        void *dh = nullptr;
+        TS_CUDA(cudaHostGetDevicePointer(&dh, p->hmem, 0));
+        unsigned char *d = static_cast<unsigned char *>(dh);
+        unsigned char *hb = static_cast<unsigned char *>(p->hmem);
+        p->dh_reqs = reinterpret_cast<ReqDesc *>(d + (reinterpret_cast<unsigned char *>(p->h_reqs) - hb));
+        p->dh_run = reinterpret_cast<uint32_t *>(d + (reinterpret_cast<unsigned char *>(p->h_run) - hb));
+        p->dh_out = reinterpret_cast<BatchOut *>(d + (reinterpret_cast<unsigned char *>(p->h_out) - hb));
+        p->dh_row0 = reinterpret_cast<unsigned long long *>(
+            d + (reinterpret_cast<unsigned char *>(p->h_row0) - hb));
+    }
     if (s) {
         p->stream = s;
     } else {
@@ -293,22 +316,21 @@ static ts_status enqueue_run(BatchPlan *p, cudaStream_t s, bool write)
     const PipeCaps &k = p->caps;
     const PipeBufs &b = p->b;
     const bool grid = p->ix->kind == TS_INDEX_SPATIAL;
-    TS_CUDA(cudaMemcpyAsync(p->d_reqs, p->h_reqs, sizeof(ReqDesc) * k.nreq,
-                            cudaMemcpyHostToDevice, s));
-    TS_CUDA(cudaMemcpyAsync(p->d_run, p->h_run, 16, cudaMemcpyHostToDevice, s));
-    const unsigned gblocks = (unsigned)std::min<uint64_t>((k.nq + TPB - 1) / TPB, 152 * 16);
-    k_gather_queries<<<gblocks, TPB, 0, s>>>(p->d_reqs, p->d_run, k.nreq, k.nq, p->d_cat);
-    TS_LAUNCHED();
-    const double *cols[8];
-    for (int c = 0; c < 8; c++) cols[c] = p->d_cat + (uint64_t)c * k.nq;
+    {
+        const uint64_t words = (uint64_t)k.nreq * (sizeof(ReqDesc) / 4);
+        const unsigned sb = (unsigned)std::min<uint64_t>((words + TPB - 1) / TPB + 1, 64);
+        k_run_start<<<sb, TPB, 0, s>>>(p->dh_reqs, p->dh_run, p->d_reqs, p->d_run, k.nreq, b);
+        TS_LAUNCHED();
+    }
     // every stage below sizes its work from the run's counts in device memory (the header and
-    // the run header), not from the plan's capacities
-    TS_CHECK(pipe_prepare(p->ix, cols, k.nq, p->d_reqs, k.nreq, b, k, s));
+    // the run header), not from the plan's capacities; the queries are read through the
+    // request table
+    TS_CHECK(pipe_prepare(p->ix, nullptr, k.nq, p->d_reqs, k.nreq, b, k, s));
     if (grid) {
         TS_CHECK(scan_u32(b.qnu, b.quoff, k.nq, b.status, s, p->d_run));
         TS_CHECK(pipe_grid_units(p->ix, k.nq, b, k, s));
     }
-    TS_CHECK(pipe_group(p->ix, p->d_reqs, k.nreq, b, k, s));
+    TS_CHECK(pipe_group(p->ix, p->d_reqs, k.nreq, b, k, false, s));
     TS_CUDA(record_ev(p->ev[0], s));
     TS_CHECK(pipe_count(p->ix, p->d_reqs, b, k, s));
     TS_CUDA(record_ev(p->ev[1], s));
@@ -318,13 +340,8 @@ static ts_status enqueue_run(BatchPlan *p, cudaStream_t s, bool write)
         TS_CHECK(pipe_write(p->ix, p->d_reqs, b, k, s));
         TS_CUDA(record_ev(p->ev[3], s));
     }
-    k_req_rows<<<1, 256, 0, s>>>(p->d_run, k.nreq, k.tiles, b, p->d_row0);
+    k_req_rows<<<1, 256, 0, s>>>(p->d_run, k.nreq, k.tiles, b, p->dh_row0, p->dh_out);
     TS_LAUNCHED();
-    TS_CUDA(cudaMemcpyAsync(p->h_out->hdr, b.hdr, sizeof(uint32_t) * 8, cudaMemcpyDeviceToHost, s));
-    TS_CUDA(cudaMemcpyAsync(p->h_out->stats, b.stats, sizeof(unsigned long long) * ST_NSLOTS,
-                            cudaMemcpyDeviceToHost, s));
-    TS_CUDA(cudaMemcpyAsync(&p->h_out->status, b.status, 4, cudaMemcpyDeviceToHost, s));
-    TS_CUDA(cudaMemcpyAsync(p->h_row0, p->d_row0, 8 * (k.nreq + 1), cudaMemcpyDeviceToHost, s));
     return TS_OK;
 }
 

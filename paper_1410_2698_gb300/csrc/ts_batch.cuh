@@ -30,8 +30,6 @@ struct BatchPlan {
     size_t dbytes = 0;
     ReqDesc *d_reqs = nullptr;
     uint32_t *d_run = nullptr;
-    double *d_cat = nullptr;
-    unsigned long long *d_row0 = nullptr;
     // mapped pinned host memory (one allocation)
     void *hmem = nullptr;
     size_t hbytes = 0;
@@ -40,6 +38,11 @@ struct BatchPlan {
     double *h_stage = nullptr;
     BatchOut *h_out = nullptr;
     unsigned long long *h_row0 = nullptr;
+    // the same mapped pinned memory as device pointers
+    ReqDesc *dh_reqs = nullptr;
+    uint32_t *dh_run = nullptr;
+    BatchOut *dh_out = nullptr;
+    unsigned long long *dh_row0 = nullptr;
     // execution
     cudaStream_t stream = nullptr;
     bool own_stream = false;

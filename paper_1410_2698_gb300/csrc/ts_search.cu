@@ -167,9 +167,10 @@ __global__ void k_qprep(PrepParams P)
         const ReqDesc R = P.reqs[r];
         double v[8];
         bool fin = true;
+        const uint64_t li = i - R.q_first;  // index within the request
 #pragma unroll
         for (int k = 0; k < 8; k++) {
-            v[k] = P.f[k][i];
+            v[k] = P.f[0] ? P.f[k][i] : R.cols[k][li];
             fin = fin && isfinite(v[k]);
         }
         if (!fin || !(v[7] > v[3])) atomicOr(P.b.status, DEV_ERR_INVALID);
@@ -486,8 +487,15 @@ __global__ void k_hdr(uint64_t gcap, uint64_t tcap, PipeBufs b)
 __global__ void k_tile_desc(uint64_t gcap, uint64_t tcap, uint32_t tile, PipeBufs b)
 {
     const uint32_t G = b.hdr[HDR_G];
-    const uint64_t T = (uint64_t)b.hdr[HDR_T_LO] | ((uint64_t)b.hdr[HDR_T_HI] << 32);
-    if (T > tcap || T > PK_MAX_TILES) return;  // overflow flagged by the header kernel
+    const uint64_t T = b.tile_base[min((uint64_t)G, gcap)];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // the run header's tile count (as k_hdr)
+        b.hdr[HDR_T_LO] = (uint32_t)T;
+        b.hdr[HDR_T_HI] = (uint32_t)(T >> 32);
+        b.stats[ST_GROUPS] = G;
+        b.stats[ST_TILES] = T;
+        if (T > tcap || T > PK_MAX_TILES) atomicOr(b.status, DEV_ERR_OVERFLOW);
+    }
+    if (T > tcap || T > PK_MAX_TILES) return;
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G && g < gcap;
@@ -1067,12 +1075,16 @@ ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq
                        const ReqDesc *reqs, uint32_t nreq, const PipeBufs &b, const PipeCaps &c,
                        cudaStream_t s)
 {
-    TS_CUDA(cudaMemsetAsync(b.stats, 0, sizeof(unsigned long long) * ST_NSLOTS, s));
-    TS_CUDA(cudaMemsetAsync(b.status, 0, sizeof(uint32_t), s));
-    TS_CUDA(cudaMemsetAsync(b.counters, 0, sizeof(uint32_t) * 2, s));
-    TS_CUDA(cudaMemsetAsync(b.req_units, 0, sizeof(uint32_t) * nreq, s));
+    // cols == nullptr: every request's columns are read through its descriptor, and the run's
+    // counters were reset by the caller
+    if (cols) {
+        TS_CUDA(cudaMemsetAsync(b.stats, 0, sizeof(unsigned long long) * ST_NSLOTS, s));
+        TS_CUDA(cudaMemsetAsync(b.status, 0, sizeof(uint32_t), s));
+        TS_CUDA(cudaMemsetAsync(b.counters, 0, sizeof(uint32_t) * 2, s));
+        TS_CUDA(cudaMemsetAsync(b.req_units, 0, sizeof(uint32_t) * nreq, s));
+    }
     PrepParams P;
-    for (int k = 0; k < 8; k++) P.f[k] = cols[k];
+    for (int k = 0; k < 8; k++) P.f[k] = cols ? cols[k] : nullptr;
     P.nq = nq;
     P.kind = ix->kind;
     P.reqs = reqs;
@@ -1123,7 +1135,7 @@ ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const
 }
 
 ts_status pipe_group(const Index *ix, const ReqDesc *reqs, uint32_t nreq, const PipeBufs &b,
-                     const PipeCaps &c,
+                     const PipeCaps &c, bool host_tiles,
                      cudaStream_t s)
 {
     // one bit above the key fields: a unit without candidates has key ~0 and sorts last
@@ -1137,8 +1149,10 @@ ts_status pipe_group(const Index *ix, const ReqDesc *reqs, uint32_t nreq, const 
                                   b);
     TS_LAUNCHED();
     TS_CHECK(scan_u32_to_u64(b.ntiles, b.tile_base, c.groups, s, b.hdr + HDR_G));
-    k_hdr<<<1, 1, 0, s>>>(c.groups, c.tiles, b);
-    TS_LAUNCHED();
+    if (host_tiles) {  // the caller reads the tile count before the count pass
+        k_hdr<<<1, 1, 0, s>>>(c.groups, c.tiles, b);
+        TS_LAUNCHED();
+    }
     return TS_OK;
 }
 
@@ -1342,7 +1356,7 @@ ts_status plain_prepare(const Index *ix, const double *const cols[8], uint64_t n
     b.ntiles = w.ntiles.as<uint32_t>();
     b.tile_base = w.tile_base.as<uint64_t>();
     c.tiles = ~0ull;  // sized after the grouping; no overflow check in the header kernel
-    TS_CHECK(pipe_group(ix, w.reqdesc.as<ReqDesc>(), 1, b, c, s));
+    TS_CHECK(pipe_group(ix, w.reqdesc.as<ReqDesc>(), 1, b, c, true, s));
     return TS_OK;
 }
 

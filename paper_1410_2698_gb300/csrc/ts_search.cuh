@@ -123,7 +123,7 @@ ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq
 ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const PipeCaps &c,
                           cudaStream_t s);
 ts_status pipe_group(const Index *ix, const ReqDesc *reqs, uint32_t nreq, const PipeBufs &b,
-                     const PipeCaps &c,
+                     const PipeCaps &c, bool host_tiles,
                      cudaStream_t s);
 ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,
                      cudaStream_t s);
