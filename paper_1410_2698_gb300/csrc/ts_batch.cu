@@ -39,6 +39,7 @@ static_assert(sizeof(ReqDesc) % 4 == 0, "the request table is copied as 32-bit w
 __global__ void k_run_start(const ReqDesc *h_reqs, const uint32_t *h_run, ReqDesc *d_reqs,
                             uint32_t *d_run, uint32_t nreq_cap, PipeBufs b)
 {
+    pdl_enter();
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t words = (uint64_t)nreq_cap * (sizeof(ReqDesc) / 4);
@@ -62,6 +63,7 @@ __global__ void k_run_start(const ReqDesc *h_reqs, const uint32_t *h_run, ReqDes
 __global__ void k_req_rows(const uint32_t *run, uint32_t nreq_cap, uint64_t tcap, PipeBufs b,
                            unsigned long long *row0, BatchOut *out)
 {
+    pdl_enter();
     const uint32_t nreq = min(run[1], nreq_cap);
     const uint64_t T = (uint64_t)b.hdr[HDR_T_LO] | ((uint64_t)b.hdr[HDR_T_HI] << 32);
     const bool ok = T <= tcap;
@@ -319,8 +321,8 @@ static ts_status enqueue_run(BatchPlan *p, cudaStream_t s, bool write)
     {
         const uint64_t words = (uint64_t)k.nreq * (sizeof(ReqDesc) / 4);
         const unsigned sb = (unsigned)std::min<uint64_t>((words + TPB - 1) / TPB + 1, 64);
-        k_run_start<<<sb, TPB, 0, s>>>(p->dh_reqs, p->dh_run, p->d_reqs, p->d_run, k.nreq, b);
-        TS_LAUNCHED();
+        TS_LAUNCH_PDL(k_run_start, dim3(sb), dim3(TPB), 0, s,
+                      p->dh_reqs, p->dh_run, p->d_reqs, p->d_run, k.nreq, b);
     }
     // every stage below sizes its work from the run's counts in device memory (the header and
     // the run header), not from the plan's capacities; the queries are read through the
@@ -340,8 +342,8 @@ static ts_status enqueue_run(BatchPlan *p, cudaStream_t s, bool write)
         TS_CHECK(pipe_write(p->ix, p->d_reqs, b, k, s));
         TS_CUDA(record_ev(p->ev[3], s));
     }
-    k_req_rows<<<1, 256, 0, s>>>(p->d_run, k.nreq, k.tiles, b, p->dh_row0, p->dh_out);
-    TS_LAUNCHED();
+    TS_LAUNCH_PDL(k_req_rows, dim3(1), dim3(256), 0, s,
+                  p->d_run, k.nreq, k.tiles, b, p->dh_row0, p->dh_out);
     return TS_OK;
 }
 

@@ -14,6 +14,7 @@
 
 #include <cstring>
 #include <string>
+#include <utility>
 
 #include "../../include/ts.h"
 
@@ -157,6 +158,41 @@ void note_launch();
     do {                                                                               \
         ::ts::note_launch();                                                           \
         TS_CUDA(cudaGetLastError());                                                   \
+    } while (0)
+
+// Programmatic dependent launch: a kernel launched with launch_pdl may be scheduled while its
+// predecessor on the stream is still running. Every such kernel starts with pdl_enter(): it
+// waits there until the predecessor grid has completed and its memory is visible (so it reads
+// nothing early), then lets its own successor be scheduled (which happens only once every block
+// of this grid has started, so early successors never hold the SMs this grid still needs).
+// Launched without the attribute, pdl_enter() returns at once.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
+#define TS_LAUNCH_PDL(...)                                                             \
+    do {                                                                               \
+        ::ts::note_launch();                                                           \
+        TS_CUDA(::ts::launch_pdl(__VA_ARGS__));                                        \
     } while (0)
 
 #define TS_CHECK(st)                                                                   \

@@ -154,6 +154,7 @@ __device__ __forceinline__ uint64_t dev_count(uint64_t cap, const uint32_t *n_de
 template <class Tin, class Tout>
 __global__ void k_tile_sums(const Tin *in, uint64_t ncap, const uint32_t *n_dev, Tout *sums)
 {
+    pdl_enter();
     const uint64_t n = dev_count(ncap, n_dev);
     const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     if (base >= n) {
@@ -176,6 +177,7 @@ template <class Tin, class Tout>
 __global__ void k_tile_scan(const Tin *in, uint64_t ncap, const uint32_t *n_dev,
                             const Tout *tile_off, Tout *out)
 {
+    pdl_enter();
     const uint64_t n = dev_count(ncap, n_dev);
     const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     if (base > n) return;
@@ -210,6 +212,7 @@ template <class Tin, class Tout>
 __global__ void k_tile_scan_lb(const Tin *in, uint64_t ncap, const uint32_t *n_dev,
                                const Tout *sums, Tout *out)
 {
+    pdl_enter();
     const uint64_t n = dev_count(ncap, n_dev);
     const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     if (base > n) return;
@@ -249,26 +252,24 @@ static ts_status scan_impl(const Tin *in, Tout *out, uint64_t n, const uint32_t 
     }
     const uint64_t nt = n / SCAN_TILE + 1;
     if (nt == 1) {
-        k_tile_scan<Tin, Tout><<<1, SCAN_THREADS, 0, s>>>(in, n, n_dev, nullptr, out);
-        TS_LAUNCHED();
+        TS_LAUNCH_PDL(k_tile_scan<Tin, Tout>, dim3(1), dim3(SCAN_THREADS), 0, s,
+                      in, n, n_dev, nullptr, out);
         return TS_OK;
     }
     DevBuf sums;
     TS_CHECK(sums.alloc(sizeof(Tout) * nt, s));
-    k_tile_sums<Tin, Tout><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, n_dev, sums.as<Tout>());
-    TS_LAUNCHED();
+    TS_LAUNCH_PDL(k_tile_sums<Tin, Tout>, dim3((unsigned)nt), dim3(SCAN_THREADS), 0, s,
+                  in, n, n_dev, sums.as<Tout>());
     if (nt <= SCAN_LOOKBACK) {
-        k_tile_scan_lb<Tin, Tout><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, n_dev,
-                                                                        sums.as<Tout>(), out);
-        TS_LAUNCHED();
+        TS_LAUNCH_PDL(k_tile_scan_lb<Tin, Tout>, dim3((unsigned)nt), dim3(SCAN_THREADS), 0, s,
+                      in, n, n_dev, sums.as<Tout>(), out);
         return TS_OK;
     }
     DevBuf offs;
     TS_CHECK(offs.alloc(sizeof(Tout) * (nt + 1), s));
     TS_CHECK((scan_impl<Tout, Tout>(sums.as<Tout>(), offs.as<Tout>(), nt, nullptr, s)));
-    k_tile_scan<Tin, Tout><<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, n_dev, offs.as<Tout>(),
-                                                                 out);
-    TS_LAUNCHED();
+    TS_LAUNCH_PDL(k_tile_scan<Tin, Tout>, dim3((unsigned)nt), dim3(SCAN_THREADS), 0, s,
+                  in, n, n_dev, offs.as<Tout>(), out);
     return TS_OK;
 }
 
@@ -281,6 +282,7 @@ ts_status scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n, cudaStr
 __global__ void k_narrow_u64(const uint64_t *in, uint32_t *out, uint64_t ncap,
                              const uint32_t *n_dev, uint32_t *status)
 {
+    pdl_enter();
     const uint64_t n = dev_count(ncap, n_dev);
     uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i > n) return;
@@ -298,9 +300,8 @@ ts_status scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *stat
     DevBuf wide;
     TS_CHECK(wide.alloc(sizeof(uint64_t) * (n + 1), s));
     TS_CHECK(scan_u32_to_u64(in, wide.as<uint64_t>(), n, s, n_dev));
-    k_narrow_u64<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(wide.as<uint64_t>(), out, n,
-                                                                   n_dev, status);
-    TS_LAUNCHED();
+    TS_LAUNCH_PDL(k_narrow_u64, dim3((unsigned)((n + 1 + 255) / 256)), dim3(256), 0, s,
+                  wide.as<uint64_t>(), out, n, n_dev, status);
     return TS_OK;
 }
 
@@ -320,6 +321,7 @@ template <class K>
 __global__ void k_rs_hist(const K *keys, uint64_t ncap, const uint32_t *n_dev, int shift,
                           uint32_t *hist, uint32_t ntiles)
 {
+    pdl_enter();
     __shared__ uint32_t h[RS_RADIX];
     const uint64_t n = dev_count(ncap, n_dev);
     for (int i = threadIdx.x; i < RS_RADIX; i += RS_THREADS) h[i] = 0;
@@ -341,6 +343,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K *keys_in, con
                                                            int shift, const uint64_t *digit_off,
                                                            uint32_t ntiles)
 {
+    pdl_enter();
     __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
     const uint64_t n = dev_count(ncap, n_dev);
     if ((uint64_t)blockIdx.x * RS_TILE >= n) return;
@@ -406,6 +409,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter_fused(const K *keys_i
                                                                  int shift, const uint32_t *hist,
                                                                  uint32_t ntiles)
 {
+    pdl_enter();
     __shared__ uint32_t wcnt[RS_WARPS][RS_RADIX];
     __shared__ uint32_t dbase[RS_RADIX];
     const uint64_t n = dev_count(ncap, n_dev);
@@ -474,6 +478,7 @@ template <class K>
 __global__ void k_copy_kv(const K *ks, const uint32_t *vs, K *kd, uint32_t *vd, uint64_t ncap,
                           const uint32_t *n_dev)
 {
+    pdl_enter();
     const uint64_t n = dev_count(ncap, n_dev);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -500,26 +505,23 @@ static ts_status radix_sort_impl(K *keys, uint32_t *vals, uint64_t n, int bits, 
     int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_rs_hist<K><<<ntiles, RS_THREADS, 0, s>>>(ka, n, n_dev, shift, hist.as<uint32_t>(),
-                                                   ntiles);
-        TS_LAUNCHED();
+        TS_LAUNCH_PDL(k_rs_hist<K>, dim3(ntiles), dim3(RS_THREADS), 0, s, ka, n, n_dev, shift,
+                      hist.as<uint32_t>(), ntiles);
         if (fused) {
-            k_rs_scatter_fused<K><<<ntiles, RS_THREADS, 0, s>>>(ka, va, kbp, vbp, n, n_dev, shift,
-                                                                hist.as<uint32_t>(), ntiles);
+            TS_LAUNCH_PDL(k_rs_scatter_fused<K>, dim3(ntiles), dim3(RS_THREADS), 0, s, ka, va, kbp,
+                          vbp, n, n_dev, shift, hist.as<uint32_t>(), ntiles);
         } else {
             TS_CHECK(scan_u32_to_u64(hist.as<uint32_t>(), off.as<uint64_t>(), nh, s));
-            k_rs_scatter<K><<<ntiles, RS_THREADS, 0, s>>>(ka, va, kbp, vbp, n, n_dev, shift,
-                                                          off.as<uint64_t>(), ntiles);
+            TS_LAUNCH_PDL(k_rs_scatter<K>, dim3(ntiles), dim3(RS_THREADS), 0, s, ka, va, kbp, vbp,
+                          n, n_dev, shift, off.as<uint64_t>(), ntiles);
         }
-        TS_LAUNCHED();
         K *tk = ka; ka = kbp; kbp = tk;
         uint32_t *tv = va; va = vbp; vbp = tv;
     }
     if (ka != keys) {
         if (n_dev) {
             const unsigned cb = (unsigned)std::min<uint64_t>((n + 255) / 256, 152 * 8);
-            k_copy_kv<K><<<cb, 256, 0, s>>>(ka, va, keys, vals, n, n_dev);
-            TS_LAUNCHED();
+            TS_LAUNCH_PDL(k_copy_kv<K>, dim3(cb), dim3(256), 0, s, ka, va, keys, vals, n, n_dev);
         } else {
             TS_CUDA(cudaMemcpyAsync(keys, ka, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
             TS_CUDA(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));

@@ -157,6 +157,7 @@ __device__ __forceinline__ uint64_t unit_key(uint32_t r, uint32_t sel, uint32_t 
 
 __global__ void k_qprep(PrepParams P)
 {
+    pdl_enter();
     const uint64_t nq = P.b.run ? min((uint64_t)P.b.run[0], P.nq) : P.nq;
     const uint32_t nreq = P.b.run ? P.b.run[1] : P.nreq;
     if (blockIdx.x == 0 && threadIdx.x == 0 && P.kind != TS_INDEX_SPATIAL)
@@ -297,6 +298,7 @@ __global__ void k_qprep(PrepParams P)
 __global__ void k_grid_units(uint64_t nqcap, uint64_t ucap, KeyFmt kf, uint32_t g,
                              const uint32_t *g_off, PipeBufs b)
 {
+    pdl_enter();
     const unsigned FULL = 0xffffffffu;
     const uint64_t nq = b.run ? min((uint64_t)b.run[0], nqcap) : nqcap;
     if (blockIdx.x == 0 && threadIdx.x == 0)
@@ -341,6 +343,7 @@ __global__ void k_grid_units(uint64_t nqcap, uint64_t ucap, KeyFmt kf, uint32_t 
 // Per request: unit starts (exclusive scan of its unit count) and group starts (ceil(units/32)).
 __global__ void k_req_scan(uint32_t nreq_cap, PipeBufs b)
 {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const uint32_t nreq = b.run ? min(b.run[1], nreq_cap) : nreq_cap;
     uint32_t us = 0, gs = 0;
@@ -366,6 +369,7 @@ __global__ void k_req_scan(uint32_t nreq_cap, PipeBufs b)
 __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, uint32_t align_sels,
                          const ReqDesc *reqs, PipeBufs b)
 {
+    pdl_enter();
     // (also writes the members' records, in the group's order, for the pair kernel)
     const unsigned FULL = 0xffffffffu;
     const uint32_t nreq = b.run ? min(b.run[1], nreq_cap) : nreq_cap;
@@ -474,6 +478,7 @@ __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, uint32
 
 __global__ void k_hdr(uint64_t gcap, uint64_t tcap, PipeBufs b)
 {
+    pdl_enter();
     const uint64_t T = b.tile_base[min((uint64_t)b.hdr[HDR_G], gcap)];
     b.hdr[HDR_T_LO] = (uint32_t)T;
     b.hdr[HDR_T_HI] = (uint32_t)(T >> 32);
@@ -486,6 +491,7 @@ __global__ void k_hdr(uint64_t gcap, uint64_t tcap, PipeBufs b)
 // that the pair kernel finds a tile's group, records and request with a single load.
 __global__ void k_tile_desc(uint64_t gcap, uint64_t tcap, uint32_t tile, PipeBufs b)
 {
+    pdl_enter();
     const uint32_t G = b.hdr[HDR_G];
     const uint64_t T = b.tile_base[min((uint64_t)G, gcap)];
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // the run header's tile count (as k_hdr)
@@ -577,6 +583,7 @@ __device__ __noinline__ bool exact_test(const QueryD *qp, const SegD *ep, bool i
 template <int PASS>
 __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P)
 {
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
@@ -924,6 +931,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
 // overflowed (the write pass sweeps instead) or the rows exceed the output capacity.
 __global__ void k_place(PipeBufs b, uint64_t scap, uint64_t tcap, uint64_t rows_cap)
 {
+    pdl_enter();
     const unsigned long long n = b.stats[ST_SCRATCH];
     if (n > scap) return;
     const uint64_t T = (uint64_t)b.hdr[HDR_T_LO] | ((uint64_t)b.hdr[HDR_T_HI] << 32);
@@ -1116,8 +1124,8 @@ ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq
     P.g = ix->g;
     P.b = b;
     if (nq) {
-        k_qprep<<<nblk(nq), TPB, 0, s>>>(P);
-        TS_LAUNCHED();
+        TS_LAUNCH_PDL(k_qprep, dim3(nblk(nq)), dim3(TPB), 0, s,
+                      P);
     }
     (void)c;
     return TS_OK;
@@ -1129,8 +1137,8 @@ ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const
     (void)c;
     if (!nq) return TS_OK;
     const unsigned ublk = (unsigned)std::min<uint64_t>((nq * 32 + TPB - 1) / TPB, 152 * 16);
-    k_grid_units<<<ublk, TPB, 0, s>>>(nq, c.units, key_fmt(ix), ix->g, ix->g_off, b);
-    TS_LAUNCHED();
+    TS_LAUNCH_PDL(k_grid_units, dim3(ublk), dim3(TPB), 0, s,
+                  nq, c.units, key_fmt(ix), ix->g, ix->g_off, b);
     return TS_OK;
 }
 
@@ -1142,16 +1150,15 @@ ts_status pipe_group(const Index *ix, const ReqDesc *reqs, uint32_t nreq, const 
     const KeyFmt f = key_fmt(ix);
     const int bits = f.lo_bits + f.sel_bits + bits_for(nreq > 1 ? nreq - 1 : 0) + 1;
     TS_CHECK(radix_sort_u64(b.keys, b.vals, c.units, bits, s, b.hdr + HDR_NU));
-    k_req_scan<<<1, 32, 0, s>>>(nreq, b);
-    TS_LAUNCHED();
+    TS_LAUNCH_PDL(k_req_scan, dim3(1), dim3(32), 0, s,
+                  nreq, b);
     const unsigned gblk = (unsigned)std::min<uint64_t>((c.groups * 32 + TPB - 1) / TPB, 152 * 16);
-    k_groups<<<gblk, TPB, 0, s>>>(nreq, c.groups, c.tile, ix->tbox ? (1u << SEL_T) : 0u, reqs,
-                                  b);
-    TS_LAUNCHED();
+    TS_LAUNCH_PDL(k_groups, dim3(gblk), dim3(TPB), 0, s,
+                  nreq, c.groups, c.tile, ix->tbox ? (1u << SEL_T) : 0u, reqs, b);
     TS_CHECK(scan_u32_to_u64(b.ntiles, b.tile_base, c.groups, s, b.hdr + HDR_G));
     if (host_tiles) {  // the caller reads the tile count before the count pass
-        k_hdr<<<1, 1, 0, s>>>(c.groups, c.tiles, b);
-        TS_LAUNCHED();
+        TS_LAUNCH_PDL(k_hdr, dim3(1), dim3(1), 0, s,
+                      c.groups, c.tiles, b);
     }
     return TS_OK;
 }
@@ -1166,10 +1173,10 @@ ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
     fill_pair_params(P, ix, reqs, b, c);
     if (c.tiles) {
         const unsigned dblk = (unsigned)std::min<uint64_t>((c.groups * 32 + TPB - 1) / TPB, 152 * 16);
-        k_tile_desc<<<dblk, TPB, 0, s>>>(c.groups, c.tiles, c.tile, b);
-        TS_LAUNCHED();
-        k_pair<PASS_COUNT><<<blocks, PK_THREADS, sizeof(WarpSmem) * PK_WARPS, s>>>(P);
-        TS_LAUNCHED();
+        TS_LAUNCH_PDL(k_tile_desc, dim3(dblk), dim3(TPB), 0, s,
+                      c.groups, c.tiles, c.tile, b);
+        TS_LAUNCH_PDL(k_pair<PASS_COUNT>, dim3(blocks), dim3(PK_THREADS),
+                      sizeof(WarpSmem) * PK_WARPS, s, P);
     }
     return TS_OK;
 }
@@ -1189,11 +1196,11 @@ ts_status pipe_write(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
     fill_pair_params(P, ix, reqs, b, c);
     if (c.tiles) {
         if (c.scratch) {
-            k_place<<<152 * 4, TPB, 0, s>>>(b, c.scratch, c.tiles, c.rows);
-            TS_LAUNCHED();
+            TS_LAUNCH_PDL(k_place, dim3(152 * 4), dim3(TPB), 0, s,
+                          b, c.scratch, c.tiles, c.rows);
         }
-        k_pair<PASS_WRITE><<<blocks, PK_THREADS, sizeof(WarpSmem) * PK_WARPS, s>>>(P);
-        TS_LAUNCHED();
+        TS_LAUNCH_PDL(k_pair<PASS_WRITE>, dim3(blocks), dim3(PK_THREADS),
+                      sizeof(WarpSmem) * PK_WARPS, s, P);
     }
     return TS_OK;
 }
