@@ -22,16 +22,6 @@ namespace {
 
 constexpr int TPB = 256;
 
-__device__ __forceinline__ uint32_t req_of_b(const ReqDesc *reqs, uint32_t nreq, uint64_t i)
-{
-    uint32_t lo = 0, hi = nreq;  // last r with q_first <= i
-    while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) / 2;
-        if (reqs[mid].q_first <= i) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
 static_assert(sizeof(ReqDesc) % 4 == 0, "the request table is copied as 32-bit words");
 
 // Start of a run: the request table and the run header come from the plan's mapped pinned

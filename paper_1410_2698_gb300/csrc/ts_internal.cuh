@@ -123,22 +123,6 @@ __host__ __device__ inline int part_of(double x, double lo, double w, int v)
     return j;
 }
 
-// The same part with the first guess taken from a precomputed reciprocal inv_w ~ 1 / w (a
-// multiplication instead of a division); the exact boundary comparisons correct the guess, so
-// the result equals part_of's.
-__host__ __device__ inline int part_of_r(double x, double lo, double w, double inv_w, int v)
-{
-    if (!(x >= lo)) return -1;
-    if (v <= 1 || !(w > 0.0)) return v - 1;
-    double f = floor((x - lo) * inv_w);
-    int j;
-    if (!(f < (double)v)) j = v - 1;
-    else if (f < 0.0) j = 0;
-    else j = (int)f;
-    while (j + 1 < v && part_bound(lo, w, j + 1) <= x) j++;
-    while (j > 0 && part_bound(lo, w, j) > x) j--;
-    return j;
-}
 
 // ---------------------------------------------------------------------------------------------
 // host-side error plumbing
