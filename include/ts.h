@@ -246,9 +246,10 @@ ts_status ts_batch_create(const ts_index *idx, const ts_batch_params *params, vo
                           ts_batch **out);
 
 /* Enqueue one run of nreq <= max_requests requests on `stream` (the plan's stream when NULL).
- * Query columns may be device pointers or host pointers (on_host = 1; copied into the plan's
- * pinned staging by this call). Returns without waiting for the device. The plan's previous run
- * must have been waited for. */
+ * Query columns may be device pointers or host pointers (on_host = 1). Host columns in pinned
+ * (page-locked) memory are read by the device in place and must stay valid until ts_batch_wait;
+ * other host columns are copied into the plan's pinned staging by this call. Returns without
+ * waiting for the device. The plan's previous run must have been waited for. */
 ts_status ts_batch_run(ts_batch *b, uint32_t nreq, const ts_segments *qs,
                        const ts_query_params *qps, void *stream);
 

@@ -53,16 +53,19 @@ def make_segments(segs):
         s.n = n
         s.on_host = 1
         keep = arrs
-    else:  # torch tensors on the GPU
+    else:  # torch tensors: on the GPU, or in (pinned) host memory
         import torch
         n = int(first.shape[0])
+        on_gpu = bool(first.is_cuda)
         for name, t in zip(FIELDS8, cols):
-            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
-                    and t.is_contiguous() and t.dim() == 1 and int(t.shape[0]) == n):
-                raise ValueError("device columns must be contiguous 1-D float64 CUDA tensors")
+            if not (isinstance(t, torch.Tensor) and bool(t.is_cuda) == on_gpu
+                    and t.dtype == torch.float64 and t.is_contiguous() and t.dim() == 1
+                    and int(t.shape[0]) == n):
+                raise ValueError("tensor columns must be contiguous 1-D float64 tensors, all on "
+                                 "the GPU or all on the host")
             setattr(s, name, t.data_ptr() if n else None)
         s.n = n
-        s.on_host = 0
+        s.on_host = 0 if on_gpu else 1
         keep = cols
     return s, keep
 
@@ -387,13 +390,21 @@ class BatchPlan:
         check(lib.ts_batch_request_rows(self._h, r, ctypes.byref(first), ctypes.byref(count)))
         return int(first.value), int(count.value)
 
-    def request_to_host(self, r, sort=False) -> dict:
+    def request_to_host(self, r, sort=False, out=None) -> dict:
+        """Copy request r's rows to host arrays: new numpy arrays, or the first rows of `out`
+        (a dict of q_idx, e_idx, t_in, t_out arrays, e.g. views of pinned buffers, large
+        enough for the rows)."""
         lib = _lib.load()
         first, n = self.request_rows(r)
-        q = np.empty(n, dtype=np.uint32)
-        e = np.empty(n, dtype=np.uint32)
-        tin = np.empty(n, dtype=np.float64)
-        tout = np.empty(n, dtype=np.float64)
+        if out is not None:
+            if any(len(out[k]) < n for k in ("q_idx", "e_idx", "t_in", "t_out")):
+                raise ValueError(f"output buffers hold fewer than the request's {n} rows")
+            q, e, tin, tout = (out[k][:n] for k in ("q_idx", "e_idx", "t_in", "t_out"))
+        else:
+            q = np.empty(n, dtype=np.uint32)
+            e = np.empty(n, dtype=np.uint32)
+            tin = np.empty(n, dtype=np.float64)
+            tout = np.empty(n, dtype=np.float64)
         if n:
             check(lib.ts_batch_copy_rows(self._h, first, n, q.ctypes.data, e.ctypes.data,
                                          tin.ctypes.data, tout.ctypes.data))

@@ -223,6 +223,8 @@ ts_status create_plan(const Index *ix, const ts_batch_params *prm, cudaStream_t 
         p->dh_out = reinterpret_cast<BatchOut *>(d + (reinterpret_cast<unsigned char *>(p->h_out) - hb));
         p->dh_row0 = reinterpret_cast<unsigned long long *>(
             d + (reinterpret_cast<unsigned char *>(p->h_row0) - hb));
+        p->dh_stage =
+            reinterpret_cast<double *>(d + (reinterpret_cast<unsigned char *>(p->h_stage) - hb));
     }
     if (s) {
         p->stream = s;
@@ -268,9 +270,21 @@ static ts_status stage_requests(BatchPlan *p, uint32_t nreq, const ts_segments *
                 return TS_ERR_INVALID_ARG;
             }
             if (qs[r].on_host) {
+                // pinned (page-locked, mapped) host columns are read by the device in place;
+                // other host memory is copied into the plan's mapped staging area
+                cudaPointerAttributes pa;
+                void *dev = nullptr;
+                if (qs[r].n && cudaPointerGetAttributes(&pa, src[c]) == cudaSuccess &&
+                    pa.type == cudaMemoryTypeHost &&
+                    cudaHostGetDevicePointer(&dev, const_cast<double *>(src[c]), 0) ==
+                        cudaSuccess) {
+                    R.cols[c] = static_cast<const double *>(dev);
+                    continue;
+                }
+                cudaGetLastError();  // (pageable memory: not an error)
                 double *dst = p->h_stage + (uint64_t)c * k.nq + first;
                 if (qs[r].n) memcpy(dst, src[c], sizeof(double) * qs[r].n);
-                R.cols[c] = dst;  // mapped pinned memory: readable by the device
+                R.cols[c] = p->dh_stage + (uint64_t)c * k.nq + first;
             } else {
                 R.cols[c] = src[c];
             }

@@ -43,6 +43,7 @@ struct BatchPlan {
     uint32_t *dh_run = nullptr;
     BatchOut *dh_out = nullptr;
     unsigned long long *dh_row0 = nullptr;
+    double *dh_stage = nullptr;
     // execution
     cudaStream_t stream = nullptr;
     bool own_stream = false;

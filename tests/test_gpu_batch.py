@@ -66,18 +66,32 @@ def test_plan_runs_equal_plain(use_graph):
     idx = api.ts_build_index(w.db, kind="spatiotemporal")
     plan = api.BatchPlan(idx, max_requests=16, max_queries=4000, max_rows=400000,
                          use_graph=use_graph)
-    for trial in range(3):
+    pinned_out = {k: torch.empty(400000, dtype=dt, pin_memory=True).numpy()
+                  for k, dt in (("q_idx", torch.int32), ("e_idx", torch.int32),
+                                ("t_in", torch.float64), ("t_out", torch.float64))}
+    for k in ("q_idx", "e_idx"):
+        pinned_out[k] = pinned_out[k].view(np.uint32)
+    for trial in range(4):
         reqs = _requests(w, rng, 6)
         if trial == 2:  # device-resident query columns
             reqs = [({f: torch.from_numpy(np.ascontiguousarray(getattr(q, f))).cuda()
                       for f in Segments.FIELDS} if q.n else q, d, ts, te)
                     for q, d, ts, te in reqs]
+        if trial == 3:  # pinned host columns (read in place) mixed with pageable ones (staged)
+            reqs = [({f: torch.from_numpy(np.ascontiguousarray(getattr(q, f))).pin_memory()
+                      for f in Segments.FIELDS} if r % 2 == 0 and q.n else q, d, ts, te)
+                    for r, (q, d, ts, te) in enumerate(reqs)]
         plan.run(reqs)
         st = plan.wait()
         assert not st["overflow"] and st["nreq"] == len(reqs)
         total = 0
         for r, req in enumerate(reqs):
-            got = plan.request_to_host(r, sort=True)
+            if trial == 3:  # rows into preallocated pinned buffers
+                got = {k: v.copy() for k, v in plan.request_to_host(r, out=pinned_out).items()}
+                o = np.lexsort((got["e_idx"], got["q_idx"]))
+                got = {k: v[o] for k, v in got.items()}
+            else:
+                got = plan.request_to_host(r, sort=True)
             q, d, ts, te = req
             qh = q if isinstance(q, Segments) else Segments(
                 *[q[f].cpu().numpy() for f in Segments.FIELDS], traj=np.zeros(0, np.uint32))
