@@ -294,8 +294,8 @@ def run_gpu(args):
     def make_plan(k, own_stream, pair_blocks=None):
         rows = (rows_per_batch[k] + rows_per_batch[k] // 20 + (1 << 20)) if serial else \
             max(1 << 20, 2 * rows_per_batch[k])
-        if pair_blocks is None:
-            pair_blocks = tuned[k]["pair_blocks"] if k in tuned else args.pair_blocks
+        if pair_blocks is None:  # an explicit --pair-blocks overrides the tuned grid
+            pair_blocks = args.pair_blocks or (tuned[k]["pair_blocks"] if k in tuned else 0)
         return api.BatchPlan(indexes[k], max_requests=len(reqs),
                              max_queries=w.queries.n * len(reqs), max_rows=rows, use_graph=True,
                              stream=0 if own_stream else None,
@@ -479,8 +479,9 @@ def run_gpu(args):
     line["config"]["plans"] = "one at a time" if serial else "resident together, overlapped"
     if tuned:
         line["config"]["autotuned"] = {k: {"index": v["index"], "tile_records": v["tile_records"],
-                                           "pair_blocks": v["pair_blocks"]
-                                           if step_pair_blocks is None else step_pair_blocks}
+                                           "pair_blocks": args.pair_blocks or (
+                                               v["pair_blocks"] if step_pair_blocks is None
+                                               else step_pair_blocks)}
                                        for k, v in tuned.items()}
     if not args.no_e2e:
         most = max(rows_per_batch.values()) if rows_per_batch else 0

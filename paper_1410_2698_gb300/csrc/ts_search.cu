@@ -202,7 +202,7 @@ __global__ void k_qprep(PrepParams P)
                                         __fadd_ru(fmx[2], R.d_up), __double2float_ru(q.w1));
 
         uint32_t sel = SEL_T, lo = 0, hi = 0;
-        bool subbin = false;
+        bool subbin = false, unit = false;
         if (P.kind == TS_INDEX_SPATIAL) {
             // cells of the grid (single assignment by MBB minimum corner) that can hold an entry
             // within d: minimum corners in [min - d - longest, max + d] per axis
@@ -271,19 +271,25 @@ __global__ void k_qprep(PrepParams P)
                     }
                 }
             }
-            const bool unit = valid && hi > lo;
+            unit = valid && hi > lo;
             P.b.u_q[i] = (uint32_t)i;
             P.b.u_lo[i] = lo;
             P.b.u_hi[i] = hi;
             P.b.u_sel[i] = sel;
             P.b.keys[i] = unit ? unit_key(r, sel, lo, P.kf) : ~0ull;
             P.b.vals[i] = (uint32_t)i;
-            if (unit) atomicAdd(&P.b.req_units[r], 1u);
         }
         const unsigned am = __activemask();
         const unsigned vm = __ballot_sync(am, valid);
         const unsigned sm = __ballot_sync(am, subbin);
         const int lane = threadIdx.x & 31;
+        if (P.kind != TS_INDEX_SPATIAL) {
+            // units per request: one atomic per request present in the warp (requests are
+            // contiguous runs of queries, so nearly always one)
+            const unsigned peers = __match_any_sync(am, r);
+            const unsigned um = __ballot_sync(am, unit) & peers;
+            if (um && lane == __ffs(peers) - 1) atomicAdd(&P.b.req_units[r], (uint32_t)__popc(um));
+        }
         if (lane == __ffs(am) - 1) {
             if (vm) atomicAdd(&P.b.stats[ST_QSEGS], (unsigned long long)__popc(vm));
             if (sm) atomicAdd(&P.b.stats[ST_SUBBIN], (unsigned long long)__popc(sm));
@@ -293,8 +299,10 @@ __global__ void k_qprep(PrepParams P)
 
 // Grid index: one unit per (cx, cy) of a query's cell box, covering cells cz_a..cz_b (a z-run
 // of the row-major cell order, contiguous in the lookup array).
-// One warp per query segment, the lanes over the (cx, cy) columns of its cell box (row-major: the
-// unit of column c is quoff[i] + c), so the two offset loads of every column run in parallel.
+// One warp per 32 consecutive query segments: the lanes first load their query's cell box and
+// unit slots (query i owns slots quoff[i] .. quoff[i] + qnu[i] - 1, so the warp's slots are one
+// contiguous range), then run over the warp's slots 32 at a time, each lane finding the query of
+// its slot among the lanes' starts; the unit counts per request are summed in the warp.
 __global__ void k_grid_units(uint64_t nqcap, uint64_t ucap, KeyFmt kf, uint32_t g,
                              const uint32_t *g_off, PipeBufs b)
 {
@@ -305,35 +313,66 @@ __global__ void k_grid_units(uint64_t nqcap, uint64_t ucap, KeyFmt kf, uint32_t 
         b.hdr[HDR_NU] = (uint32_t)min((uint64_t)b.quoff[nq], ucap);  // unit slots of the runs
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nq; i += warps) {
-        const uint32_t nu = b.qnu[i];
-        if (!nu) continue;
-        const uint32_t u0 = b.quoff[i];
-        if ((uint64_t)u0 + nu > ucap) {  // more runs than the unit buffers hold
-            if (lane == 0) atomicOr(b.status, DEV_ERR_OVERFLOW);
-            continue;
-        }
-        const uint32_t r = b.qreq[i];
-        const uint32_t w0 = b.qcell[2 * i], w1 = b.qcell[2 * i + 1];
-        const uint32_t ax = w0 & 1023u, ay = (w0 >> 10) & 1023u, az = (w0 >> 20) & 1023u;
-        const uint32_t by = (w1 >> 10) & 1023u, bz = (w1 >> 20) & 1023u;
-        const uint32_t ny = by - ay + 1;
-        uint32_t nvalid = 0;
-        for (uint32_t c = lane; c < nu; c += 32) {
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < nq;
+         w += warps) {
+        const uint64_t i = w * 32 + lane;
+        const bool has = i < nq;
+        const uint32_t nu = has ? b.qnu[i] : 0u;
+        // lanes past the last query start beyond every slot
+        const uint32_t u0 = has ? b.quoff[i] : 0xffffffffu;
+        const uint32_t r = has ? b.qreq[i] : 0u;
+        const uint32_t c0 = has ? b.qcell[2 * i] : 0u, c1 = has ? b.qcell[2 * i + 1] : 0u;
+        const int last = (int)min((uint64_t)31, nq - 1 - w * 32);
+        const uint32_t ubeg = __shfl_sync(FULL, u0, 0);
+        const uint32_t uend = __shfl_sync(FULL, u0 + nu, last);
+        uint32_t cr = 0, cn = 0;  // this lane's running (request, valid units)
+        for (uint32_t base = ubeg; base < uend; base += 32) {
+            const uint32_t u = base + (uint32_t)lane;
+            // the last lane whose start is at or before u owns slot u (a query without slots
+            // shares its start with the next query, which then owns it)
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step; step >>= 1) {
+                const uint32_t cand = __shfl_sync(FULL, u0, j + step);
+                if (cand <= u) j += step;
+            }
+            const uint32_t ju0 = __shfl_sync(FULL, u0, j);
+            const uint32_t jr = __shfl_sync(FULL, r, j);
+            const uint32_t w0 = __shfl_sync(FULL, c0, j), w1 = __shfl_sync(FULL, c1, j);
+            if (u >= uend) continue;
+            if (u >= ucap) {  // more runs than the unit buffers hold
+                atomicOr(b.status, DEV_ERR_OVERFLOW);
+                continue;
+            }
+            const uint32_t ax = w0 & 1023u, ay = (w0 >> 10) & 1023u, az = (w0 >> 20) & 1023u;
+            const uint32_t by = (w1 >> 10) & 1023u, bz = (w1 >> 20) & 1023u;
+            const uint32_t ny = by - ay + 1;
+            const uint32_t c = u - ju0;
             const uint32_t cx = ax + c / ny, cy = ay + c % ny;
-            const uint32_t u = u0 + c;
             const uint64_t row = ((uint64_t)cx * g + cy) * g;
             const uint32_t lo = g_off[row + az], hi = g_off[row + bz + 1];
-            b.u_q[u] = (uint32_t)i;
+            b.u_q[u] = (uint32_t)(w * 32 + (uint64_t)j);
             b.u_lo[u] = lo;
             b.u_hi[u] = hi;
             b.u_sel[u] = SEL_GRID;
-            b.keys[u] = hi > lo ? unit_key(r, SEL_GRID, lo, kf) : ~0ull;
+            b.keys[u] = hi > lo ? unit_key(jr, SEL_GRID, lo, kf) : ~0ull;
             b.vals[u] = u;
-            nvalid += hi > lo;
+            if (jr != cr) {  // a request boundary inside the warp's slots (rare)
+                if (cn) atomicAdd(&b.req_units[cr], cn);
+                cr = jr;
+                cn = 0;
+            }
+            cn += hi > lo;
         }
-        for (int o = 16; o; o >>= 1) nvalid += __shfl_xor_sync(FULL, nvalid, o);
-        if (lane == 0 && nvalid) atomicAdd(&b.req_units[r], nvalid);
+        // nearly always one request per warp: one atomic for the warp
+        const uint32_t r0 = __shfl_sync(FULL, cr, 0);
+        if (__all_sync(FULL, cr == r0 || cn == 0)) {
+            uint32_t tot = cn;
+            for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(FULL, tot, o);
+            if (lane == 0 && tot) atomicAdd(&b.req_units[r0], tot);
+        } else if (cn) {
+            atomicAdd(&b.req_units[cr], cn);
+        }
     }
 }
 
@@ -395,7 +434,7 @@ __global__ void k_groups(uint32_t nreq_cap, uint64_t gcap, uint32_t tile, uint32
             b.g_first[g] = first;
             b.g_count[g] = n;
             const ReqDesc &R = reqs[r];
-            b.ghdr[g] = make_float4(R.d_dn, R.d2u, __uint_as_float(R.q_first), 0.0f);
+            b.ghdr[g] = make_float4(R.d_dn, R.d2u, __uint_as_float(R.q_first), __uint_as_float(r));
         }
         // key = (array, start); lanes past the group's members hold the largest key
         uint64_t key = ~0ull;
@@ -502,19 +541,28 @@ __global__ void k_tile_desc(uint64_t gcap, uint64_t tcap, uint32_t tile, PipeBuf
         if (T > tcap || T > PK_MAX_TILES) atomicOr(b.status, DEV_ERR_OVERFLOW);
     }
     if (T > tcap || T > PK_MAX_TILES) return;
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G && g < gcap;
          g += warps) {
-        const uint32_t first = b.g_first[g], count = b.g_count[g];
+        const uint32_t count = b.g_count[g];
         if (!count) continue;
-        const uint32_t r = b.qreq[b.u_q[b.vals[first]]];
+        const uint32_t r = __float_as_uint(b.ghdr[g].w);
         const uint64_t base = b.tile_base[g];
         const uint32_t nseg = b.g_nseg[g];
+        // lane k holds segment k (one round of loads for all the group's segments)
+        uint32_t slo = 0, shi = 0, ssel = 0, st0 = 0;
+        if ((uint32_t)lane < nseg) {
+            const uint64_t o = (uint64_t)g * GROUP + lane;
+            slo = b.seg_lo[o];
+            shi = b.seg_hi[o];
+            ssel = b.seg_sel[o];
+            st0 = b.seg_t0[o];
+        }
         for (uint32_t k = 0; k < nseg; k++) {
-            const uint64_t o = (uint64_t)g * GROUP + k;
-            const uint32_t lo = b.seg_lo[o], hi = b.seg_hi[o], sel = b.seg_sel[o];
-            const uint32_t t0 = b.seg_t0[o];
+            const uint32_t lo = __shfl_sync(FULL, slo, k), hi = __shfl_sync(FULL, shi, k);
+            const uint32_t sel = __shfl_sync(FULL, ssel, k), t0 = __shfl_sync(FULL, st0, k);
             const uint32_t n = (hi - lo + tile - 1) / tile;
             for (uint32_t j = lane; j < n; j += 32) {
                 const uint32_t s0 = lo + j * tile;
@@ -533,7 +581,7 @@ __global__ void k_tile_desc(uint64_t gcap, uint64_t tcap, uint32_t tile, PipeBuf
 struct __align__(16) WarpSmem {
     RecF stage[2][PK_CH];
     MemberRec mem[GROUP];  // the tile's group members
-    float4 ghdr;           // their request's d_dn, d2u, q_first
+    float4 ghdr;           // their request's d_dn, d2u, q_first (and the request)
     uint4 dnext;           // the next tile's descriptor (asynchronous copy during the sweep)
     RecF cbox[32];         // bounding records of the tile's chunks (arrays that have them)
     // exact-test queue, first in first out, carried from tile to tile: query index in the batch,
@@ -1051,16 +1099,19 @@ int bits_for(uint64_t v)
 // ---------------------------------------------------------------------------------------------
 // pipeline stages
 // ---------------------------------------------------------------------------------------------
-KeyFmt key_fmt(const Index *ix)
+KeyFmt key_fmt(const Index *ix, uint32_t nreq)
 {
     uint64_t maxlen = ix->n;
     for (int d = 0; d < 3; d++) maxlen = std::max<uint64_t>(maxlen, ix->st_len[d]);
     maxlen = std::max<uint64_t>(maxlen, ix->g_len);
     KeyFmt f;
-    const int full = bits_for(maxlen);  // bits of a range start
-    f.lo_bits = std::min(full, KEY_LO_BITS);
-    f.lo_shift = full - f.lo_bits;
     f.sel_bits = ix->kind == TS_INDEX_SPATIOTEMPORAL ? 2 : 0;  // X, Y, Z or T
+    const int full = bits_for(maxlen);  // bits of a range start
+    // as many start bits as keep the whole key (with the request and guard bits) within two
+    // 8-bit radix passes, but no fewer than KEY_LO_MIN and no more than KEY_LO_BITS
+    const int fit = 16 - 1 - f.sel_bits - bits_for(nreq > 1 ? nreq - 1 : 0);
+    f.lo_bits = std::min(full, std::max(KEY_LO_MIN, std::min(KEY_LO_BITS, fit)));
+    f.lo_shift = full - f.lo_bits;
     return f;
 }
 
@@ -1097,7 +1148,7 @@ ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq
     P.kind = ix->kind;
     P.reqs = reqs;
     P.nreq = nreq;
-    P.kf = key_fmt(ix);
+    P.kf = key_fmt(ix, c.nreq);
     P.n = ix->n;
     P.m = ix->m;
     P.tmin = ix->tmin;
@@ -1127,18 +1178,16 @@ ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq
         TS_LAUNCH_PDL(k_qprep, dim3(nblk(nq)), dim3(TPB), 0, s,
                       P);
     }
-    (void)c;
     return TS_OK;
 }
 
 ts_status pipe_grid_units(const Index *ix, uint64_t nq, const PipeBufs &b, const PipeCaps &c,
                           cudaStream_t s)
 {
-    (void)c;
     if (!nq) return TS_OK;
-    const unsigned ublk = (unsigned)std::min<uint64_t>((nq * 32 + TPB - 1) / TPB, 152 * 16);
+    const unsigned ublk = (unsigned)std::min<uint64_t>((nq + TPB - 1) / TPB, 152 * 16);
     TS_LAUNCH_PDL(k_grid_units, dim3(ublk), dim3(TPB), 0, s,
-                  nq, c.units, key_fmt(ix), ix->g, ix->g_off, b);
+                  nq, c.units, key_fmt(ix, c.nreq), ix->g, ix->g_off, b);
     return TS_OK;
 }
 
@@ -1147,8 +1196,8 @@ ts_status pipe_group(const Index *ix, const ReqDesc *reqs, uint32_t nreq, const 
                      cudaStream_t s)
 {
     // one bit above the key fields: a unit without candidates has key ~0 and sorts last
-    const KeyFmt f = key_fmt(ix);
-    const int bits = f.lo_bits + f.sel_bits + bits_for(nreq > 1 ? nreq - 1 : 0) + 1;
+    const KeyFmt f = key_fmt(ix, c.nreq);
+    const int bits = f.lo_bits + f.sel_bits + bits_for(c.nreq > 1 ? c.nreq - 1 : 0) + 1;
     TS_CHECK(radix_sort_u64(b.keys, b.vals, c.units, bits, s, b.hdr + HDR_NU));
     TS_LAUNCH_PDL(k_req_scan, dim3(1), dim3(32), 0, s,
                   nreq, b);

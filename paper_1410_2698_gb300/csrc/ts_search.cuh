@@ -135,7 +135,8 @@ struct KeyFmt {
     int lo_bits = 0, lo_shift = 0, sel_bits = 0;
 };
 constexpr int KEY_LO_BITS = 13;
-KeyFmt key_fmt(const Index *ix);
+constexpr int KEY_LO_MIN = 11;
+KeyFmt key_fmt(const Index *ix, uint32_t nreq);
 ts_status search_brute_noalloc(const ts_segments *db, const ts_segments *q,
                                const ts_query_params *qp, uint32_t *q_idx, uint32_t *e_idx,
                                double *t_in, double *t_out, uint64_t capacity, uint64_t *count,
