@@ -248,7 +248,7 @@ def run_gpu(args):
         from paper_1410_2698_gb300 import autotune
         treqs = [(w.queries, d, w.t_start, w.t_end) for d in w.distances]
         for k in kinds:
-            tuned[k] = autotune.tune(w.db, treqs, k, repeats=2)
+            tuned[k] = autotune.tune(w.db, treqs, k, repeats=10)
     indexes = {k: api.ts_build_index(w.db, kind=k, **(tuned[k]["index"] if k in tuned else {}))
                for k in kinds}
     qdev = {f: torch.from_numpy(getattr(w.queries, f)).to(dev) for f in Segments.FIELDS}
@@ -407,14 +407,21 @@ def run_gpu(args):
             tot[key] += st[key]
         pair_ms += st["ms_count_pass"] + st["ms_write_pass"]
         b = breakdown.setdefault(f"{k}@d={d:g}", {"tests": 0, "hits": 0, "pair_ms": 0.0,
-                                                  "exact": 0, "subbin_queries": 0})
+                                                  "exact": 0, "subbin_queries": 0, "chunks": 0,
+                                                  "dense_chunks": 0, "sparse_visits": 0,
+                                                  "stage2": 0})
+        b["chunks"] += st["n_chunks"]
+        b["dense_chunks"] += st["n_dense"]
+        b["sparse_visits"] += st["n_sparse"]
+        b["stage2"] += st["n_stage2"]
         b["tests"] += st["n_tests"]
         b["hits"] += st["n_hits"]
         b["exact"] += st["n_exact"]
         b["subbin_queries"] += st["n_subbin"]
         b["pair_ms"] += st["ms_count_pass"] + st["ms_write_pass"]
     for b in breakdown.values():
-        for key in ("tests", "hits", "exact", "subbin_queries"):
+        for key in ("tests", "hits", "exact", "subbin_queries", "chunks", "dense_chunks",
+                    "sparse_visits", "stage2"):
             b[key] //= max(args.steps, 1)
         b["pair_ms"] /= max(args.steps, 1)
     btot = {"n_qsegs": 0, "n_tests": 0, "n_hits": 0, "n_exact": 0}

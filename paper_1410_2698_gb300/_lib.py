@@ -49,7 +49,9 @@ class ts_search_stats(ctypes.Structure):
                 ("n_tests", ctypes.c_uint64), ("n_exact", ctypes.c_uint64),
                 ("n_hits", ctypes.c_uint64), ("n_tiles", ctypes.c_uint64),
                 ("n_groups", ctypes.c_uint64), ("n_subbin", ctypes.c_uint64),
-                ("ms_count_pass", ctypes.c_double), ("ms_write_pass", ctypes.c_double)]
+                ("ms_count_pass", ctypes.c_double), ("ms_write_pass", ctypes.c_double),
+                ("n_chunks", ctypes.c_uint64), ("n_dense", ctypes.c_uint64),
+                ("n_sparse", ctypes.c_uint64), ("n_stage2", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: (float(getattr(self, k)) if k.startswith("ms_") else int(getattr(self, k)))

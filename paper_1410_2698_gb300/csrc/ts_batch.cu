@@ -400,6 +400,10 @@ static void fill_stats(const BatchOut *o, ts_search_stats *s)
     s->n_tiles = o->stats[ST_TILES];
     s->n_groups = o->stats[ST_GROUPS];
     s->n_subbin = o->stats[ST_SUBBIN];
+    s->n_chunks = o->stats[ST_CHUNKS];
+    s->n_dense = o->stats[ST_DENSE];
+    s->n_sparse = o->stats[ST_SPARSE];
+    s->n_stage2 = o->stats[ST_STAGE2];
 }
 
 ts_status plan_wait(BatchPlan *p, ts_batch_status *out)

@@ -589,6 +589,8 @@ struct __align__(16) WarpSmem {
     uint32_t q_qi[PK_QUEUE], q_pos[PK_QUEUE], q_tile[PK_QUEUE], q_ql[PK_QUEUE];
     unsigned long long bar[2];
     unsigned long long mbar;  // members + chunk boxes
+    // sweep counts of the count pass: chunks, bitmask chunks, sparse member visits, survivors
+    unsigned long long sweep[4];
 };
 
 enum { PASS_COUNT = 0, PASS_WRITE = 1 };
@@ -641,6 +643,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
     const PipeBufs &B = P.b;
 
     if (lane == 0) {
+        for (int k = 0; k < 4; k++) W.sweep[k] = 0;
         mbar_init(&W.bar[0], 1);
         mbar_init(&W.bar[1], 1);
         mbar_init(&W.mbar, 1);
@@ -862,6 +865,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             }
             parity[st] ^= 1u;
             pending[st] = false;
+            if (PASS == PASS_COUNT && lane == 0) W.sweep[0]++;
             const uint32_t cs = s0 + c * PK_CH;
             const uint32_t cn = min((uint32_t)PK_CH, s1 - cs);
             const bool mine = (mc >> c) & 1u;
@@ -879,6 +883,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             if (!act) {
                 // (a chunk copied ahead of the member tests that no member meets)
             } else if (__popc(act) <= PK_SPARSE) {
+                if (PASS == PASS_COUNT && lane == 0) W.sweep[2] += __popc(act);
                 // few members meet this chunk: one lane per slot (slots lane and lane + 32), the
                 // members that meet the chunk in turn, their boxes read as broadcasts
                 const bool in0 = (uint32_t)lane < cn, in1 = (uint32_t)lane + 32 < cn;
@@ -905,6 +910,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 // warp-uniform address, a shared-memory broadcast); bit i is set when the axis
                 // extents overlap. Four independent accumulators per half keep the OR chains
                 // short.
+                if (PASS == PASS_COUNT && lane == 0) W.sweep[1]++;
                 const float2 *ax = reinterpret_cast<const float2 *>(&W.stage[st][0]) + dim;
                 uint32_t a[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
@@ -919,7 +925,9 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             // filters and into the exact-test queue
             for (;;) {
                 const bool have = (m0 | m1) != 0u;
-                if (!__any_sync(FULL, have)) break;
+                const unsigned hv = __ballot_sync(FULL, have);
+                if (!hv) break;
+                if (PASS == PASS_COUNT && lane == 0) W.sweep[3] += __popc(hv);
                 bool p = false;
                 uint32_t i = 0;
                 if (have) {
@@ -967,6 +975,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
     if (PASS == PASS_COUNT) {
         for (int o = 16; o; o >>= 1) acc_tests += __shfl_xor_sync(FULL, acc_tests, o);
         if (lane == 0) {
+            for (int k = 0; k < 4; k++) atomicAdd(&B.stats[ST_CHUNKS + k], W.sweep[k]);
             atomicAdd(&B.stats[ST_TESTS], acc_tests);
             atomicAdd(&B.stats[ST_EXACT], acc_exact);
             atomicAdd(&B.stats[ST_HITS], acc_hits);
@@ -1429,6 +1438,10 @@ ts_status copy_stats(const PipeBufs &b, cudaStream_t s, ts_search_stats *st, uin
     st->n_tiles = h[ST_TILES];
     st->n_groups = h[ST_GROUPS];
     st->n_subbin = h[ST_SUBBIN];
+    st->n_chunks = h[ST_CHUNKS];
+    st->n_dense = h[ST_DENSE];
+    st->n_sparse = h[ST_SPARSE];
+    st->n_stage2 = h[ST_STAGE2];
     return TS_OK;
 }
 
