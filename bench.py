@@ -12,6 +12,7 @@ cores, on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -32,6 +33,23 @@ FP64_PEAK_TFLOPS = 1.25                              # GB300 FP64 (nominal)
 PREFILTER_FLOPS = 20       # FP32 flops per candidate test (6 sub, 6 max, 1 mul + 2 fma, 3 cmp)
 EXACT_FLOPS = 41           # FP64 flops per exact test (window, positions, a, b, c, decision)
 INTERVAL_FLOPS = 10        # FP64 flops per hit for the roots (sqrt, 2 div, clamps)
+# DRAM traffic of the pair kernel per launch (count and write passes of the three plans, averaged
+# over the launches of the timed one-plan-at-a-time loop): dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of this bench on a GB300, valid while the kernel's
+# sources hash to `sources` (otherwise the line reports null)
+PAIR_TRAFFIC = {
+    "random-walk-1m": {"bytes_per_launch": 23073941, "sources": "2222dc5b543790d1",
+                       "capture": "profiles/k_pair_random-walk-1m_batched.md"},
+}
+PAIR_SOURCES = ("ts_search.cu", "ts_search.cuh", "ts_internal.cuh", "ts_device.cuh")
+
+
+def pair_source_hash():
+    h = hashlib.sha256()
+    for f in PAIR_SOURCES:
+        with open(os.path.join(ROOT, "paper_1410_2698_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -457,6 +475,12 @@ def run_gpu(args):
     else:
         roof = roofline(tot, pair_ms, peaks)
         roof["timed_form"] = "plain"
+    cap = PAIR_TRAFFIC.get(w.name)
+    if cap and cap["sources"] == pair_source_hash():
+        roof["traffic"] = cap["bytes_per_launch"]
+        roof["traffic_capture"] = cap["capture"]
+    else:
+        roof["traffic_capture"] = "none for the current kernel sources"
     # whole-job aggregates (every rank processes the same amount of work)
     value = btot["n_qsegs"] * world / (batch_total / 1e3)
     line = {
@@ -701,10 +725,25 @@ def cpu_baseline(w, budget_s=8.0):
         if take == nq:
             break
         take = min(nq, take * 2)
-    return {"value": qsegs / spent, "unit": "query segs/s", "cores": threads, "kind": "oracle",
-            "tests_per_s": tests / spent,
-            "sample": f"{rounds} passes over the first up-to-{take} query segments x "
-                      f"{len(w.distances)} distances ({spent:.1f} s of CPU time)"}
+    out = {"value": qsegs / spent, "unit": "query segs/s", "cores": threads, "kind": "oracle",
+           "tests_per_s": tests / spent,
+           "sample": f"{rounds} passes over the first up-to-{take} query segments x "
+                     f"{len(w.distances)} distances ({spent:.1f} s of CPU time)"}
+    # the same oracle on one core, on a smaller sample (the first distance only)
+    take1 = min(nq, 200)
+    sub = w.queries.take(np.arange(take1))
+    spent1 = qsegs1 = tests1 = 0
+    while spent1 < budget_s / 4:
+        t0 = time.perf_counter()
+        _, nt, nqs = oracle.search_count(w.db, sub, w.t_start, w.t_end, w.distances[0], threads=1)
+        spent1 += time.perf_counter() - t0
+        qsegs1 += nqs
+        tests1 += nt
+    out["single_thread"] = {"value": qsegs1 / spent1, "unit": "query segs/s", "cores": 1,
+                            "tests_per_s": tests1 / spent1,
+                            "sample": f"the first {take1} query segments at d = "
+                                      f"{w.distances[0]:g} ({spent1:.1f} s)"}
+    return out
 
 
 def run_reference(args):

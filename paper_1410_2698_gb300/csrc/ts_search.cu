@@ -579,7 +579,7 @@ __global__ void k_tile_desc(uint64_t gcap, uint64_t tcap, uint32_t tile, PipeBuf
 // pair kernel
 // ---------------------------------------------------------------------------------------------
 struct __align__(16) WarpSmem {
-    RecF stage[2][PK_CH];
+    RecF stage[PK_STAGES][PK_CH];
     MemberRec mem[GROUP];  // the tile's group members
     float4 ghdr;           // their request's d_dn, d2u, q_first (and the request)
     uint4 dnext;           // the next tile's descriptor (asynchronous copy during the sweep)
@@ -587,7 +587,7 @@ struct __align__(16) WarpSmem {
     // exact-test queue, first in first out, carried from tile to tile: query index in the batch,
     // entry position in its sorted array, tile | sel << 29, query index within its request
     uint32_t q_qi[PK_QUEUE], q_pos[PK_QUEUE], q_tile[PK_QUEUE], q_ql[PK_QUEUE];
-    unsigned long long bar[2];
+    unsigned long long bar[PK_STAGES];
     unsigned long long mbar;  // members + chunk boxes
     // sweep counts of the count pass: chunks, bitmask chunks, sparse member visits, survivors
     unsigned long long sweep[4];
@@ -625,9 +625,9 @@ __device__ __noinline__ bool exact_test(const QueryD *qp, const SegD *ep, bool i
 
 // Persistent pair kernel. Warps take tiles (a group of up to 32 query units and up to `tile`
 // consecutive entries of one sorted array) from a device counter. Entry records stream through
-// a two-stage shared-memory buffer filled by 1-D bulk copies. The conservative FP32 filters pick
-// the candidates of the exact FP64 test; those wait in a per-warp queue that is carried across
-// tiles and drained 32 at a time, so that the FP64 instructions run on full warps.
+// a ring of PK_STAGES shared-memory buffers filled by 1-D bulk copies. The conservative FP32
+// filters pick the candidates of the exact FP64 test; those wait in a per-warp queue that is
+// carried across tiles and drained 32 at a time, so that the FP64 instructions run on full warps.
 // Count pass: hits per tile. Write pass: the rows of every tile with hits, at its offset from the
 // scan, in queue order (the same order in both passes, so the offsets match).
 template <int PASS>
@@ -644,14 +644,18 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
 
     if (lane == 0) {
         for (int k = 0; k < 4; k++) W.sweep[k] = 0;
-        mbar_init(&W.bar[0], 1);
-        mbar_init(&W.bar[1], 1);
+        for (int k = 0; k < PK_STAGES; k++) mbar_init(&W.bar[k], 1);
         mbar_init(&W.mbar, 1);
         fence_mbar_init();
     }
     __syncwarp();
-    uint32_t parity[2] = {0u, 0u}, mparity = 0u;
-    bool pending[2] = {false, false}, mpending = false;
+    uint32_t parity[PK_STAGES], mparity = 0u;
+    bool pending[PK_STAGES], mpending = false;
+#pragma unroll
+    for (int k = 0; k < PK_STAGES; k++) {
+        parity[k] = 0u;
+        pending[k] = false;
+    }
     bool abort = false;
 
     uint64_t ntiles = (uint64_t)B.hdr[HDR_T_LO] | ((uint64_t)B.hdr[HDR_T_HI] << 32);
@@ -772,15 +776,15 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             bulk_g2s(&W.ghdr, B.ghdr + g, (uint32_t)sizeof(float4), &W.mbar);
             bulk_g2s(&W.mem[0], B.gmem + (uint64_t)g * GROUP, mb, &W.mbar);
             if (bx) bulk_g2s(&W.cbox[0], bx + s0 / PK_CH, cb, &W.mbar);
-            for (uint32_t c = 0; c < 2 && c < nch; c++) {
+            for (uint32_t c = 0; c < (uint32_t)PK_STAGES && c < nch; c++) {
                 const uint32_t cs = s0 + c * PK_CH, cn = min((uint32_t)PK_CH, s1 - cs);
                 mbar_arrive_tx(&W.bar[c], cn * (uint32_t)sizeof(RecF));
                 bulk_g2s(&W.stage[c][0], recs + cs, cn * (uint32_t)sizeof(RecF), &W.bar[c]);
             }
         }
         mpending = true;
-        pending[0] = nch > 0;
-        pending[1] = nch > 1;
+#pragma unroll
+        for (int k = 0; k < PK_STAGES; k++) pending[k] = nch > (uint32_t)k;
         if (!mbar_wait_bounded(&W.mbar, mparity)) {
             abort = true;
             break;
@@ -850,15 +854,17 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             if (bx && meet) meet = filter_box(W.cbox[c], ea, eb);
             mc |= (uint32_t)meet << c;
         }
-        // chunks to sweep, in order; the first two were copied already, later ones are copied
-        // two sweeps ahead, so a chunk no member meets is neither copied nor swept
+        // chunks to sweep, in order; the first PK_STAGES were copied already, later ones are
+        // copied PK_STAGES sweeps ahead, so a chunk no member meets is neither copied nor swept
         const uint32_t need = __reduce_or_sync(FULL, mc);
-        uint32_t todo = need | (nch > 1 ? 3u : 1u);
-        uint32_t pend = todo & ~3u;
+        const uint32_t first =
+            nch >= (uint32_t)PK_STAGES ? (1u << PK_STAGES) - 1u : (1u << nch) - 1u;
+        uint32_t todo = need | first;
+        uint32_t pend = todo & ~((1u << PK_STAGES) - 1u);
         for (uint32_t k = 0; todo && !abort; k++) {
             const uint32_t c = __ffs(todo) - 1;
             todo &= todo - 1u;
-            const int st = k & 1;
+            const int st = (int)(k % PK_STAGES);
             if (!mbar_wait_bounded(&W.bar[st], parity[st])) {
                 abort = true;
                 break;
@@ -968,7 +974,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
     if (abort) {
         if (lane == 0) atomicOr(B.status, DEV_ERR_TIMEOUT);
         // let copies still in flight land before the shared memory is released
-        for (int st = 0; st < 2; st++)
+        for (int st = 0; st < PK_STAGES; st++)
             if (pending[st]) mbar_wait_bounded(&W.bar[st], parity[st]);
         if (mpending) mbar_wait_bounded(&W.mbar, mparity);
     }
