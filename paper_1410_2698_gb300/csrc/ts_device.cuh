@@ -145,8 +145,12 @@ static __device__ __forceinline__ void quad_interval(const Quad &k, double *tin,
 // ea = (xmin - d, ymin - d, zmin - d, w0) rounded down; eb = (xmax + d, ..., w1) rounded up.
 static __device__ __forceinline__ bool filter_box(const RecF &r, const float4 &ea, const float4 &eb)
 {
-    return (r.t0 < eb.w) && (r.t1 > ea.w) && (r.xmax >= ea.x) && (r.xmin <= eb.x) &&
-           (r.ymax >= ea.y) && (r.ymin <= eb.y) && (r.zmax >= ea.z) && (r.zmin <= eb.z);
+    // four independent axis tests, combined as a tree (no short-circuit chain)
+    const bool t = (r.t0 < eb.w) & (r.t1 > ea.w);
+    const bool x = (r.xmax >= ea.x) & (r.xmin <= eb.x);
+    const bool y = (r.ymax >= ea.y) & (r.ymin <= eb.y);
+    const bool z = (r.zmax >= ea.z) & (r.zmin <= eb.z);
+    return (t & x) & (y & z);
 }
 
 // Stage 2: the squared distance between the entry MBB and the query MBB with every subtraction,

@@ -904,10 +904,11 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                     const float4 mea = M.ea, meb = M.eb;
                     const uint32_t mq = M.qi, mlo = M.lo;
                     const uint32_t w = M.hi - mlo;
-                    bool p0 = (pos0 - mlo) < w && filter_box(r0, mea, meb);
-                    bool p1 = (pos1 - mlo) < w && filter_box(r1, mea, meb);
-                    p0 = p0 && filter_gap_e(r0, mea, meb, d_dn, d2u);
-                    p1 = p1 && filter_gap_e(r1, mea, meb, d_dn, d2u);
+                    bool p0 = ((pos0 - mlo) < w) & filter_box(r0, mea, meb);
+                    bool p1 = ((pos1 - mlo) < w) & filter_box(r1, mea, meb);
+                    if (!__any_sync(FULL, p0 | p1)) continue;  // (the common case)
+                    p0 = p0 & filter_gap_e(r0, mea, meb, d_dn, d2u);
+                    p1 = p1 & filter_gap_e(r1, mea, meb, d_dn, d2u);
                     enqueue(p0, mq, pos0);
                     enqueue(p1, mq, pos1);
                 }
@@ -945,7 +946,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                         m1 &= m1 - 1u;
                     }
                     const RecF r = W.stage[st][i];
-                    p = filter_box(r, ea, eb) && filter_gap_e(r, ea, eb, d_dn, d2u);
+                    p = filter_box(r, ea, eb) & filter_gap_e(r, ea, eb, d_dn, d2u);
                 }
                 enqueue(p, myq, cs + i);
             }
