@@ -848,11 +848,17 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         // the chunks this lane's member meets: its range overlaps the chunk and, for an array
         // with chunk boxes, its expanded box meets the chunk's bounding record
         uint32_t mc = 0u;
-        for (uint32_t c = 0; c < nch; c++) {
-            const uint32_t cs = s0 + c * PK_CH, ce = min(cs + (uint32_t)PK_CH, s1);
-            bool meet = lo < ce && hi > cs;
-            if (bx && meet) meet = filter_box(W.cbox[c], ea, eb);
-            mc |= (uint32_t)meet << c;
+        if (bx) {
+            for (uint32_t c = 0; c < nch; c++) {
+                const uint32_t cs = s0 + c * PK_CH, ce = min(cs + (uint32_t)PK_CH, s1);
+                const bool meet = (lo < ce) & (hi > cs) & filter_box(W.cbox[c], ea, eb);
+                mc |= (uint32_t)meet << c;
+            }
+        } else {
+            for (uint32_t c = 0; c < nch; c++) {
+                const uint32_t cs = s0 + c * PK_CH, ce = min(cs + (uint32_t)PK_CH, s1);
+                mc |= (uint32_t)((lo < ce) & (hi > cs)) << c;
+            }
         }
         // chunks to sweep, in order; the first PK_STAGES were copied already, later ones are
         // copied PK_STAGES sweeps ahead, so a chunk no member meets is neither copied nor swept
