@@ -573,9 +573,8 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
                 t0 = time.perf_counter()
                 plan.run(reqs)
                 st = plan.wait()
-                for r in range(len(reqs)):
-                    rows = plan.request_to_host(r, out=rows_out)
-                    d2h += sum(v.nbytes for v in rows.values())
+                rows, _ = plan.rows_to_host(out=rows_out)  # every request's rows, one copy
+                d2h += sum(v.nbytes for v in rows.values())
                 torch.cuda.synchronize()
                 total_ms += (time.perf_counter() - t0) * 1e3
                 qsegs += st["stats"]["n_qsegs"]
@@ -595,9 +594,8 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
         for k in kinds:
             st = plans[k].wait()
             q_s += st["stats"]["n_qsegs"]
-            for r in range(len(reqs)):
-                rows = plans[k].request_to_host(r, out=rows_out)
-                d2h_s += sum(v.nbytes for v in rows.values())
+            rows, _ = plans[k].rows_to_host(out=rows_out)  # every request's rows, one copy
+            d2h_s += sum(v.nbytes for v in rows.values())
             h2d_s += 8 * 8 * w.queries.n * len(reqs)
         torch.cuda.synchronize()
         if s > 0:  # the first pass is warm-up

@@ -381,6 +381,7 @@ class BatchPlan:
         st = _lib.ts_batch_status()
         check(lib.ts_batch_wait(self._h, ctypes.byref(st)))
         self._keep = None
+        self._last = (int(st.nreq), int(st.rows))
         return {"rows": int(st.rows), "nreq": int(st.nreq), "overflow": bool(st.overflow),
                 "stats": st.stats.as_dict()}
 
@@ -413,6 +414,27 @@ class BatchPlan:
             order = np.lexsort((e, q))
             out = {k: v[order] for k, v in out.items()}
         return out
+
+    def rows_to_host(self, out=None):
+        """Copy every row of the last run (requests in order, each request's rows contiguous) to
+        host arrays in one call: new numpy arrays or the first rows of `out`. Returns the rows
+        and each request's (first, count) within them."""
+        nreq, total = getattr(self, "_last", (0, 0))
+        spans = [self.request_rows(r) for r in range(nreq)]
+        lib = _lib.load()
+        if out is not None:
+            if any(len(out[k]) < total for k in ("q_idx", "e_idx", "t_in", "t_out")):
+                raise ValueError(f"output buffers hold fewer than the run's {total} rows")
+            q, e, tin, tout = (out[k][:total] for k in ("q_idx", "e_idx", "t_in", "t_out"))
+        else:
+            q = np.empty(total, dtype=np.uint32)
+            e = np.empty(total, dtype=np.uint32)
+            tin = np.empty(total, dtype=np.float64)
+            tout = np.empty(total, dtype=np.float64)
+        if total:
+            check(lib.ts_batch_copy_rows(self._h, 0, total, q.ctypes.data, e.ctypes.data,
+                                         tin.ctypes.data, tout.ctypes.data))
+        return {"q_idx": q, "e_idx": e, "t_in": tin, "t_out": tout}, spans
 
     def free(self):
         if self._h:

@@ -142,6 +142,7 @@ struct PrepParams {
     const double *g_bound[3];    // grid boundary tables (g + 1 each)
     float g_iwf[3];
     double g_lo[3], g_w[3], longest[3];
+    uint32_t smem_bytes;  // > 0: the lookup tables are first copied into shared memory
     PipeBufs b;
 };
 
@@ -158,6 +159,42 @@ __device__ __forceinline__ uint64_t unit_key(uint32_t r, uint32_t sel, uint32_t 
 __global__ void k_qprep(PrepParams P)
 {
     pdl_enter();
+    // the bin, subbin and cell boundary tables the lookups read, copied into shared memory (one
+    // round of loads instead of chains of dependent global loads) when they fit
+    extern __shared__ __align__(16) unsigned char qp_smem[];
+    const double *bin_start = P.bin_start, *bin_pmax = P.bin_pmax;
+    const uint32_t *bin_off = P.bin_off;
+    const double *sub_bound[3] = {P.sub_bound[0], P.sub_bound[1], P.sub_bound[2]};
+    const double *g_bound[3] = {P.g_bound[0], P.g_bound[1], P.g_bound[2]};
+    if (P.smem_bytes) {
+        double *sd = reinterpret_cast<double *>(qp_smem);
+        const uint32_t t = threadIdx.x, nt = blockDim.x;
+        if (P.kind == TS_INDEX_SPATIAL) {
+            for (int d = 0; d < 3; d++) {
+                for (uint32_t i = t; i <= P.g; i += nt) sd[i] = P.g_bound[d][i];
+                g_bound[d] = sd;
+                sd += P.g + 1;
+            }
+        } else {
+            for (uint32_t i = t; i < P.m; i += nt) sd[i] = P.bin_start[i];
+            bin_start = sd;
+            sd += P.m;
+            for (uint32_t i = t; i < P.m; i += nt) sd[i] = P.bin_pmax[i];
+            bin_pmax = sd;
+            sd += P.m;
+            if (P.kind == TS_INDEX_SPATIOTEMPORAL) {
+                for (int d = 0; d < 3; d++) {
+                    for (uint32_t i = t; i <= P.v[d]; i += nt) sd[i] = P.sub_bound[d][i];
+                    sub_bound[d] = sd;
+                    sd += P.v[d] + 1;
+                }
+            }
+            uint32_t *so = reinterpret_cast<uint32_t *>(sd);
+            for (uint32_t i = t; i <= P.m; i += nt) so[i] = P.bin_off[i];
+            bin_off = so;
+        }
+        __syncthreads();
+    }
     const uint64_t nq = P.b.run ? min((uint64_t)P.b.run[0], P.nq) : P.nq;
     const uint32_t nreq = P.b.run ? P.b.run[1] : P.nreq;
     if (blockIdx.x == 0 && threadIdx.x == 0 && P.kind != TS_INDEX_SPATIAL)
@@ -213,8 +250,8 @@ __global__ void k_qprep(PrepParams P)
                 double a = ((mn[d] - R.d) - P.longest[d]) -
                            EXT_SLACK * ((fabs(mn[d]) + R.d) + P.longest[d]);
                 double bb = (mx[d] + R.d) + EXT_SLACK * (fabs(mx[d]) + R.d);
-                int pa = part_of_t(a, P.g_bound[d], P.g_iwf[d], (int)P.g);
-                int pb = part_of_t(bb, P.g_bound[d], P.g_iwf[d], (int)P.g);
+                int pa = part_of_t(a, g_bound[d], P.g_iwf[d], (int)P.g);
+                int pb = part_of_t(bb, g_bound[d], P.g_iwf[d], (int)P.g);
                 if (pa < 0) pa = 0;
                 if (pb < pa) any = false;
                 ca[d] = (uint32_t)pa;
@@ -229,13 +266,13 @@ __global__ void k_qprep(PrepParams P)
                     hi = (uint32_t)P.n;
                 } else {
                     // temporal range (Sec. 4.2 schedule)
-                    const uint32_t jl = first_pmax_above_b(P.bin_pmax, P.bin_start, P.m,
+                    const uint32_t jl = first_pmax_above_b(bin_pmax, bin_start, P.m,
                                                            P.bin_iwf, P.bin_back, q.w0);
-                    const int jh = last_start_below_t(P.bin_start, P.m, P.bin_iwf, q.w1);
+                    const int jh = last_start_below_t(bin_start, P.m, P.bin_iwf, q.w1);
                     const bool any = (int)jl <= jh;
                     if (any) {
-                        lo = P.bin_off[jl];
-                        hi = P.bin_off[jh + 1];
+                        lo = bin_off[jl];
+                        hi = bin_off[jh + 1];
                     }
                     if (any && P.kind == TS_INDEX_SPATIOTEMPORAL) {
                         // the dimension whose d-expanded extent meets one subbin (or none) with
@@ -246,8 +283,8 @@ __global__ void k_qprep(PrepParams P)
                             const int vv = (int)P.v[d];
                             double a = (mn[d] - R.d) - EXT_SLACK * (fabs(mn[d]) + R.d);
                             double bb = (mx[d] + R.d) + EXT_SLACK * (fabs(mx[d]) + R.d);
-                            const int pa = part_of_t(a, P.sub_bound[d], P.sub_iwf[d], vv);
-                            const int pb = part_of_t(bb, P.sub_bound[d], P.sub_iwf[d], vv);
+                            const int pa = part_of_t(a, sub_bound[d], P.sub_iwf[d], vv);
+                            const int pb = part_of_t(bb, sub_bound[d], P.sub_iwf[d], vv);
                             const int ja = pa < 0 ? 0 : pa, jb = pb;
                             uint32_t clo, chi;
                             if (jb < ja) {
@@ -1196,8 +1233,18 @@ ts_status pipe_prepare(const Index *ix, const double *const cols[8], uint64_t nq
     }
     P.g = ix->g;
     P.b = b;
+    // lookup tables in shared memory when they fit the default 48 KB
+    uint64_t tb = 0;
+    if (ix->kind == TS_INDEX_SPATIAL) {
+        tb = 3ull * 8 * ((uint64_t)ix->g + 1);
+    } else if (ix->kind != TS_INDEX_BRUTE) {
+        tb = 16ull * ix->m + 4ull * ((uint64_t)ix->m + 1);
+        if (ix->kind == TS_INDEX_SPATIOTEMPORAL)
+            for (int d = 0; d < 3; d++) tb += 8ull * ((uint64_t)ix->v[d] + 1);
+    }
+    P.smem_bytes = tb <= 48 * 1024 ? (uint32_t)tb : 0u;
     if (nq) {
-        TS_LAUNCH_PDL(k_qprep, dim3(nblk(nq)), dim3(TPB), 0, s,
+        TS_LAUNCH_PDL(k_qprep, dim3(nblk(nq)), dim3(TPB), P.smem_bytes, s,
                       P);
     }
     return TS_OK;

@@ -98,6 +98,13 @@ def test_plan_runs_equal_plain(use_graph):
             _same(got, _plain(idx, (qh, d, ts, te)))
             total += got["q_idx"].size
         assert total == st["rows"]
+        # every row of the run in one copy: each request's span equals its own copy
+        allrows, spans = plan.rows_to_host()
+        assert len(spans) == len(reqs) and sum(n for _, n in spans) == st["rows"]
+        for r, (f, n) in enumerate(spans):
+            own = plan.request_to_host(r)
+            for k in ("q_idx", "e_idx", "t_in", "t_out"):
+                assert np.array_equal(allrows[k][f:f + n], own[k]), k
     plan.free()
 
 
