@@ -38,17 +38,25 @@ INTERVAL_FLOPS = 10        # FP64 flops per hit for the roots (sqrt, 2 div, clam
 # dram__bytes_write.sum from one ncu capture of this bench on a GB300, valid while the kernel's
 # sources hash to `sources` (otherwise the line reports null)
 PAIR_TRAFFIC = {
-    "random-walk-1m": {"bytes_per_launch": 23073941, "sources": "2222dc5b543790d1",
+    "random-walk-1m": {"bytes_per_launch": 22515968, "sources": "a856d41fa7e0bec7",
                        "capture": "profiles/k_pair_random-walk-1m_batched.md"},
 }
-PAIR_SOURCES = ("ts_search.cu", "ts_search.cuh", "ts_internal.cuh", "ts_device.cuh")
+PAIR_SOURCES = ("ts_search.cuh", "ts_internal.cuh", "ts_device.cuh")
 
 
-def pair_source_hash():
+def pair_source_hash(csrc=None):
+    """Hash of the pair kernel's sources: its headers and its section of ts_search.cu (from the
+    pair kernel banner to the placement kernel)."""
+    csrc = csrc or os.path.join(ROOT, "paper_1410_2698_gb300", "csrc")
     h = hashlib.sha256()
     for f in PAIR_SOURCES:
-        with open(os.path.join(ROOT, "paper_1410_2698_gb300", "csrc", f), "rb") as fh:
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "ts_search.cu"), "rb") as fh:
+        text = fh.read()
+    a = text.index(b"\n// pair kernel\n")
+    b = text.index(b"\n// Rows of the hits the count pass kept", a)
+    h.update(text[a:b])
     return h.hexdigest()[:16]
 
 

@@ -158,9 +158,9 @@ __device__ __forceinline__ uint64_t unit_key(uint32_t r, uint32_t sel, uint32_t 
 
 __global__ void k_qprep(PrepParams P)
 {
-    pdl_enter();
     // the bin, subbin and cell boundary tables the lookups read, copied into shared memory (one
-    // round of loads instead of chains of dependent global loads) when they fit
+    // round of loads instead of chains of dependent global loads) when they fit; they belong to
+    // the index, so the copy runs before the wait on the preceding kernel
     extern __shared__ __align__(16) unsigned char qp_smem[];
     const double *bin_start = P.bin_start, *bin_pmax = P.bin_pmax;
     const uint32_t *bin_off = P.bin_off;
@@ -195,6 +195,7 @@ __global__ void k_qprep(PrepParams P)
         }
         __syncthreads();
     }
+    pdl_enter();
     const uint64_t nq = P.b.run ? min((uint64_t)P.b.run[0], P.nq) : P.nq;
     const uint32_t nreq = P.b.run ? P.b.run[1] : P.nreq;
     if (blockIdx.x == 0 && threadIdx.x == 0 && P.kind != TS_INDEX_SPATIAL)
