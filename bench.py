@@ -336,9 +336,9 @@ def run_gpu(args):
     if not serial and args.autotune and not args.pair_blocks:
         # the plans of a step overlap on their own streams, and a persistent pair kernel holds
         # the SMs it runs on: the pair grid is tuned on the overlapped step itself (all resident
-        # blocks, 1.5 or 1 block per SM), outside the timed region
+        # blocks, or 1.75 to 1 block per SM), outside the timed region
         best = None
-        for pb in (0, 228, 152):
+        for pb in (0, 266, 228, 190, 152):
             trial = {k: make_plan(k, True, pb) for k in kinds}
             for _ in range(8):  # warm-up (graph capture), then the timed trials
                 for k in kinds:

@@ -19,11 +19,11 @@ from . import api
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ts_gb300_autotune.json")
 
 SPACE = {
-    "temporal": {"t_bins": [0.5, 1, 2, 4, 8]},           # multiples of span / longest duration
+    "temporal": {"t_bins": [0.25, 0.5, 1, 2, 4, 8]},     # multiples of span / longest duration
     "spatiotemporal": {"t_bins": [1, 4], "sub_bins": [4, 8, 16, 32, 64]},
     "spatial": {"grid_cells": [10, 25, 50, 100]},
 }
-TILES = [128, 256, 512, 1024]
+TILES = [128, 256, 512, 1024, 2048]
 
 
 def signature(db, requests, kind) -> str:
