@@ -625,6 +625,7 @@ struct __align__(16) WarpSmem {
     // exact-test queue, first in first out, carried from tile to tile: query index in the batch,
     // entry position in its sorted array, tile | sel << 29, query index within its request
     uint32_t q_qi[PK_QUEUE], q_pos[PK_QUEUE], q_tile[PK_QUEUE], q_ql[PK_QUEUE];
+    uint32_t plist[PK_PLIST];  // (member << 8 | slot) pairs of a chunk that passed the box test
     unsigned long long bar[PK_STAGES];
     unsigned long long mbar;  // members + chunk boxes
     // sweep counts of the count pass: chunks, bitmask chunks, sparse member visits, survivors
@@ -942,20 +943,46 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 if (!in0) r0.t0 = INFINITY;  // a slot past the chunk never passes the filter
                 if (!in1) r1.t0 = INFINITY;
                 const uint32_t pos0 = cs + lane, pos1 = cs + 32 + lane;
+                // the (member, slot) pairs that pass the box test are listed in shared memory
+                // (member by member, slot order) and go through the gap bound one per lane, so
+                // that the gap bound and the queue run on full warps
+                uint32_t npl = 0;  // listed pairs (warp-uniform)
+                auto drain = [&]() {
+                    __syncwarp();
+                    for (uint32_t b = 0; b < npl; b += 32) {
+                        bool p = false;
+                        uint32_t mq = 0, slot = 0;
+                        if (b + lane < npl) {
+                            const uint32_t e = W.plist[b + lane];
+                            const MemberRec &M = W.mem[e >> 8];
+                            slot = e & 63u;
+                            mq = M.qi;
+                            p = filter_gap_e(W.stage[st][slot], M.ea, M.eb, d_dn, d2u);
+                        }
+                        enqueue(p, mq, cs + slot);
+                    }
+                    npl = 0;
+                    __syncwarp();
+                };
                 for (unsigned rem = act; rem; rem &= rem - 1u) {
                     // (a member in act has this tile's array: its range is its own)
-                    const MemberRec &M = W.mem[__ffs(rem) - 1];
+                    const uint32_t m = __ffs(rem) - 1;
+                    const MemberRec &M = W.mem[m];
                     const float4 mea = M.ea, meb = M.eb;
-                    const uint32_t mq = M.qi, mlo = M.lo;
+                    const uint32_t mlo = M.lo;
                     const uint32_t w = M.hi - mlo;
-                    bool p0 = ((pos0 - mlo) < w) & filter_box(r0, mea, meb);
-                    bool p1 = ((pos1 - mlo) < w) & filter_box(r1, mea, meb);
-                    if (!__any_sync(FULL, p0 | p1)) continue;  // (the common case)
-                    p0 = p0 & filter_gap_e(r0, mea, meb, d_dn, d2u);
-                    p1 = p1 & filter_gap_e(r1, mea, meb, d_dn, d2u);
-                    enqueue(p0, mq, pos0);
-                    enqueue(p1, mq, pos1);
+                    const bool p0 = ((pos0 - mlo) < w) & filter_box(r0, mea, meb);
+                    const bool p1 = ((pos1 - mlo) < w) & filter_box(r1, mea, meb);
+                    const unsigned b0 = __ballot_sync(FULL, p0), b1 = __ballot_sync(FULL, p1);
+                    if (!(b0 | b1)) continue;  // (the common case)
+                    if (p0) W.plist[npl + __popc(b0 & lt_mask)] = (m << 8) | (uint32_t)lane;
+                    if (p1)
+                        W.plist[npl + __popc(b0) + __popc(b1 & lt_mask)] =
+                            (m << 8) | (uint32_t)(lane + 32);
+                    npl += __popc(b0) + __popc(b1);
+                    if (npl > PK_PLIST - 64) drain();  // (room for one more member's 64 pairs)
                 }
+                if (npl) drain();
             } else {
                 // stage 1: one axis of every slot against every member (slot i is read at a
                 // warp-uniform address, a shared-memory broadcast); bit i is set when the axis
