@@ -25,9 +25,18 @@ def rw1m_indexes(rw1m):
         idx.free()
 
 
+_RW1M_REF = {}
+
+
+def _rw1m_ref(w, d):
+    if d not in _RW1M_REF:
+        _RW1M_REF[d] = oracle.search(w.db, w.queries, w.t_start, w.t_end, d)
+    return _RW1M_REF[d]
+
+
 @pytest.mark.parametrize("d", [1.0, 5.0, 10.0, 25.0])
 def test_random_walk_1m_full(rw1m, rw1m_indexes, d):
-    ref = oracle.search(rw1m.db, rw1m.queries, rw1m.t_start, rw1m.t_end, d)
+    ref = _rw1m_ref(rw1m, d)
     counts = {}
     for kind, idx in rw1m_indexes.items():
         got = api.ts_search(idx, rw1m.queries, d, rw1m.t_start, rw1m.t_end).to_host(sort=True)
@@ -35,6 +44,43 @@ def test_random_walk_1m_full(rw1m, rw1m_indexes, d):
         counts[kind] = got["q_idx"].size
     # every query segment meets its own database twin over its whole extent
     assert ref["q_idx"].size >= rw1m.queries.n
+
+
+@pytest.mark.parametrize("kind,params,tile", [
+    ("temporal", {"t_bins": 250}, 1024),
+    ("spatiotemporal", {"t_bins": 500, "sub_bins": 32}, 512),
+    ("spatial", {"grid_cells": 25}, 256),
+])
+def test_random_walk_1m_batched_as_benchmarked(rw1m, kind, params, tile):
+    """The benchmark's launch configuration: one plan per index with the four distances as its
+    requests, replayed as a CUDA graph on its own stream with a 228-block pair grid, index
+    parameters and tiles as the autotuner picks them on this workload; every request's rows
+    against the oracle, on the second replay."""
+    import torch
+    from paper_1410_2698_gb300.workloads import Segments
+    w = rw1m
+    qdev = {f: torch.from_numpy(getattr(w.queries, f)).cuda() for f in Segments.FIELDS}
+    reqs = [(qdev, d, w.t_start, w.t_end) for d in w.distances]
+    idx = api.ts_build_index(w.db, kind=kind, **params)
+    units = 0
+    if kind == "spatial":
+        units = sum(int(api.ts_schedule(idx, w.queries, d, w.t_start, w.t_end)[1].sum())
+                    for d in w.distances)
+        units += units // 10 + 1024
+    plan = api.BatchPlan(idx, max_requests=len(reqs), max_queries=w.queries.n * len(reqs),
+                         max_rows=1 << 20, use_graph=True, stream=0, tile_records=tile,
+                         pair_blocks=228, max_units=units, max_tiles=1 << 20)
+    try:
+        for _ in range(2):
+            plan.run(reqs, stream=0)
+            st = plan.wait()
+            assert not st["overflow"]
+        for r, d in enumerate(w.distances):
+            got = plan.request_to_host(r, sort=True)
+            parity.compare(got, _rw1m_ref(w, d), w.db, w.queries, w.t_start, w.t_end, d)
+    finally:
+        plan.free()
+        idx.free()
 
 
 def _trajectory_sample(w, n_traj, seed):
