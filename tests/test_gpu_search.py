@@ -294,3 +294,20 @@ def test_measured_alu_peaks_are_plausible():
     p = api.ts_measure_alu_peaks()
     assert 10.0 < p["fp32_tflops"] < 400.0
     assert 0.05 < p["fp64_tflops"] < p["fp32_tflops"]
+
+
+@pytest.mark.parametrize("kind", ["temporal", "spatiotemporal", "spatial"])
+def test_sweep_counters_are_consistent(tiny, kind):
+    """The count pass's sweep counters: chunks swept bound the bitmask chunks, every candidate
+    that reached the FP64 test passed the FP32 filters of a swept chunk, and the hits are among
+    the FP64 tests."""
+    w = tiny
+    idx = api.ts_build_index(w.db, kind=kind)
+    res = api.ts_search(idx, w.queries, 5.0, 0.0, 70.0)
+    st = res.stats
+    assert st["n_tests"] > 0 and st["n_chunks"] > 0
+    assert st["n_dense"] <= st["n_chunks"]
+    assert st["n_sparse"] <= 32 * st["n_chunks"]  # (at most one visit per member and chunk)
+    assert st["n_hits"] <= st["n_exact"] <= st["n_tests"]
+    res.free()
+    idx.free()
