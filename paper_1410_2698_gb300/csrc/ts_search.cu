@@ -200,6 +200,7 @@ __global__ void k_qprep(PrepParams P)
     const uint32_t nreq = P.b.run ? P.b.run[1] : P.nreq;
     if (blockIdx.x == 0 && threadIdx.x == 0 && P.kind != TS_INDEX_SPATIAL)
         P.b.hdr[HDR_NU] = (uint32_t)nq;  // one unit slot per query
+    uint32_t n_valid = 0, n_subbin = 0;  // (a warp's first active lane)
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t r = req_of(P.reqs, nreq, (uint32_t)i);
@@ -329,9 +330,26 @@ __global__ void k_qprep(PrepParams P)
             if (um && lane == __ffs(peers) - 1) atomicAdd(&P.b.req_units[r], (uint32_t)__popc(um));
         }
         if (lane == __ffs(am) - 1) {
-            if (vm) atomicAdd(&P.b.stats[ST_QSEGS], (unsigned long long)__popc(vm));
-            if (sm) atomicAdd(&P.b.stats[ST_SUBBIN], (unsigned long long)__popc(sm));
+            n_valid += __popc(vm);
+            n_subbin += __popc(sm);
         }
+    }
+    // the block's counts: one atomic per counter and block
+    __shared__ uint32_t red[2][32];
+    const int warp = threadIdx.x >> 5, lane0 = threadIdx.x & 31;
+    for (int o = 16; o; o >>= 1) {
+        n_valid += __shfl_xor_sync(0xffffffffu, n_valid, o);
+        n_subbin += __shfl_xor_sync(0xffffffffu, n_subbin, o);
+    }
+    if (lane0 == 0) {
+        red[0][warp] = n_valid;
+        red[1][warp] = n_subbin;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        unsigned long long v = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[threadIdx.x][w];
+        if (v) atomicAdd(&P.b.stats[threadIdx.x == 0 ? ST_QSEGS : ST_SUBBIN], v);
     }
 }
 
@@ -628,8 +646,9 @@ struct __align__(16) WarpSmem {
     uint32_t plist[PK_PLIST];  // (member << 8 | slot) pairs of a chunk that passed the box test
     unsigned long long bar[PK_STAGES];
     unsigned long long mbar;  // members + chunk boxes
-    // sweep counts of the count pass: chunks, bitmask chunks, sparse member visits, survivors
-    unsigned long long sweep[4];
+    // counts of the count pass: chunks, bitmask chunks, sparse member visits, survivors (then,
+    // at the end, the warp's tests, FP64 tests and hits)
+    unsigned long long sweep[8];
 };
 
 enum { PASS_COUNT = 0, PASS_WRITE = 1 };
@@ -1051,12 +1070,24 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         if (mpending) mbar_wait_bounded(&W.mbar, mparity);
     }
     if (PASS == PASS_COUNT) {
+        // the block's counts are summed in shared memory: one atomic per counter and block
+        // (warps finish together, so per-warp atomics on these few addresses would queue)
         for (int o = 16; o; o >>= 1) acc_tests += __shfl_xor_sync(FULL, acc_tests, o);
         if (lane == 0) {
-            for (int k = 0; k < 4; k++) atomicAdd(&B.stats[ST_CHUNKS + k], W.sweep[k]);
-            atomicAdd(&B.stats[ST_TESTS], acc_tests);
-            atomicAdd(&B.stats[ST_EXACT], acc_exact);
-            atomicAdd(&B.stats[ST_HITS], acc_hits);
+            W.sweep[4] = acc_tests;
+            W.sweep[5] = acc_exact;
+            W.sweep[6] = acc_hits;
+        }
+        __syncthreads();
+        if (threadIdx.x < 7) {
+            const WarpSmem *all = reinterpret_cast<const WarpSmem *>(smem_raw);
+            unsigned long long v = 0;
+            for (int w = 0; w < PK_WARPS; w++) v += all[w].sweep[threadIdx.x];
+            const int slot = threadIdx.x < 4 ? ST_CHUNKS + (int)threadIdx.x
+                                             : (threadIdx.x == 4 ? ST_TESTS
+                                                                 : (threadIdx.x == 5 ? ST_EXACT
+                                                                                     : ST_HITS));
+            if (v) atomicAdd(&B.stats[slot], v);
         }
     }
 }
