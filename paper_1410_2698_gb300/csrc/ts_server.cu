@@ -281,6 +281,8 @@ ts_status launch_slot(Server *s, Slot &sl)
 void loop(Server *s)
 {
     cudaSetDevice(s->device);
+    constexpr double SPIN_US = 2000.0;  // poll without sleeping this long after any progress
+    double spin_until = 0.0;
     std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
         bool any_busy = false;
@@ -327,13 +329,21 @@ void loop(Server *s)
             sl.busy = true;
             progressed = true;
         }
-        if (progressed) continue;
+        if (progressed) {
+            spin_until = s->now_us() + SPIN_US;
+            continue;
+        }
         any_busy = false;
         for (Slot &sl : s->slots) any_busy = any_busy || sl.busy;
         if (any_busy) {
-            // a batch is on the device: poll its completion at a short period
+            // a batch is on the device: poll its completion, yielding the core (a sleep of a few
+            // microseconds oversleeps by tens), and sleeping only once nothing has progressed
+            // for SPIN_US
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            if (s->now_us() < spin_until)
+                std::this_thread::yield();
+            else
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
             lk.lock();
         } else {
             s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
