@@ -303,6 +303,7 @@ def run_gpu(args):
     # batched form: one reusable plan per index, replayed as a CUDA graph; the distances are the
     # requests of one batch
     reqs = [(qdev, d, w.t_start, w.t_end) for d in w.distances]
+    preq = api.prepare_requests(reqs)  # marshalled once for every run of the plans
     # a plan holds its rows (24 B) and the count pass's kept hits (32 B) for max_rows rows
     plan_bytes = sum(56 * max(1 << 20, 2 * rows_per_batch[k]) for k in kinds)
     serial = args.serial_plans or plan_bytes > 60e9
@@ -342,13 +343,13 @@ def run_gpu(args):
             trial = {k: make_plan(k, True, pb) for k in kinds}
             for _ in range(8):  # warm-up (graph capture), then the timed trials
                 for k in kinds:
-                    trial[k].run(reqs, stream=0)
+                    trial[k].run(preq, stream=0)
                 for k in kinds:
                     trial[k].wait()
             t0 = time.perf_counter()
             for _ in range(20):
                 for k in kinds:
-                    trial[k].run(reqs, stream=0)
+                    trial[k].run(preq, stream=0)
                 for k in kinds:
                     trial[k].wait()
             dt = time.perf_counter() - t0
@@ -362,7 +363,7 @@ def run_gpu(args):
 
         def batched_step(collect=None):
             for k in kinds:
-                plans[k].run(reqs, stream=0)  # each plan on its own stream: the plans overlap
+                plans[k].run(preq, stream=0)  # each plan on its own stream: the plans overlap
             for k in kinds:
                 st = plans[k].wait()
                 if st["overflow"]:
@@ -389,7 +390,7 @@ def run_gpu(args):
         # the overlapped step the events of one plan also see the other plans' kernels)
         def alone_step():
             for k in kinds:
-                plans[k].run(reqs)
+                plans[k].run(preq)
                 alone.append((k, plans[k].wait()))
 
         alone_ms = _timed(args, stream, flush, alone_step, steps=min(args.steps, 20))
@@ -402,14 +403,14 @@ def run_gpu(args):
             plan = make_plan(k, False)
 
             def one(plan=plan, k=k):
-                plan.run(reqs)
+                plan.run(preq)
                 st = plan.wait()
                 if st["overflow"]:
                     raise RuntimeError(f"batch plan overflow for {k}")
                 batch_stats.append((k, st))
 
             for _ in range(max(args.warmup, 0)):
-                plan.run(reqs)
+                plan.run(preq)
                 plan.wait()
             n0 = len(batch_stats)
             a = api.ts_kernel_launches()
@@ -567,7 +568,7 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
     from paper_1410_2698_gb300.workloads import Segments
     qhost = {f: torch.from_numpy(np.ascontiguousarray(getattr(w.queries, f))).pin_memory()
              for f in Segments.FIELDS}
-    reqs = [(qhost, d, w.t_start, w.t_end) for d in w.distances]
+    reqs = api.prepare_requests([(qhost, d, w.t_start, w.t_end) for d in w.distances])
     rows_out, keep = _pinned_rows(max_rows)
     if make_plan is not None:
         total_ms, h2d, d2h, qsegs = 0.0, 0, 0, 0
@@ -586,7 +587,7 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
                 torch.cuda.synchronize()
                 total_ms += (time.perf_counter() - t0) * 1e3
                 qsegs += st["stats"]["n_qsegs"]
-                h2d += 8 * 8 * w.queries.n * len(reqs)
+                h2d += 8 * 8 * w.queries.n * reqs.n
             plan.free()
         return {"value": qsegs / (total_ms / 1e3), "unit": "query segs/s",
                 "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
@@ -604,7 +605,7 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
             q_s += st["stats"]["n_qsegs"]
             rows, _ = plans[k].rows_to_host(out=rows_out)  # every request's rows, one copy
             d2h_s += sum(v.nbytes for v in rows.values())
-            h2d_s += 8 * 8 * w.queries.n * len(reqs)
+            h2d_s += 8 * 8 * w.queries.n * reqs.n
         torch.cuda.synchronize()
         if s > 0:  # the first pass is warm-up
             ms.append((time.perf_counter() - t0) * 1e3)

@@ -335,6 +335,20 @@ def _requests(requests):
     return segs, qps, keep
 
 
+class PreparedRequests:
+    """Requests marshalled once for repeated BatchPlan.run calls (the request table is built
+    from the columns' addresses: the columns must stay alive and in place while it is used)."""
+
+    def __init__(self, requests):
+        self.n = len(requests)
+        self.segs, self.qps, self._keep = _requests(requests)
+        self._requests = list(requests)
+
+
+def prepare_requests(requests) -> PreparedRequests:
+    return PreparedRequests(requests)
+
+
 def ts_search_batch(index: Index, requests, stream=None):
     """One pipeline for many requests; returns one Result per request."""
     lib = _lib.load()
@@ -371,10 +385,16 @@ class BatchPlan:
         return self._h
 
     def run(self, requests, stream=None):
+        """Run the plan on a list of requests, or on PreparedRequests (marshalled once)."""
         lib = _lib.load()
-        segs, qps, keep = _requests(requests)
-        self._keep = (segs, qps, keep)
-        check(lib.ts_batch_run(self._h, len(requests), segs, qps, _current_stream(stream)))
+        if isinstance(requests, PreparedRequests):
+            segs, qps, n = requests.segs, requests.qps, requests.n
+            self._keep = requests
+        else:
+            segs, qps, keep = _requests(requests)
+            n = len(requests)
+            self._keep = (segs, qps, keep)
+        check(lib.ts_batch_run(self._h, n, segs, qps, _current_stream(stream)))
 
     def wait(self) -> dict:
         lib = _lib.load()
