@@ -362,6 +362,21 @@ def ts_search_batch(index: Index, requests, stream=None):
     return [Result(ctypes.c_void_p(outs[r]), st) for r in range(n)]
 
 
+class _Outcome(dict):
+    """A batch run's outcome; its "stats" entry is converted from the C struct on first use."""
+
+    def __init__(self, st):
+        super().__init__(rows=int(st.rows), nreq=int(st.nreq), overflow=bool(st.overflow))
+        self._st = st
+
+    def __missing__(self, key):
+        if key == "stats":
+            v = self._st.stats.as_dict()
+            self[key] = v
+            return v
+        raise KeyError(key)
+
+
 class BatchPlan:
     """Reusable batched pipeline with fixed capacities (ts_batch_*), optionally replayed as a
     CUDA graph."""
@@ -397,13 +412,14 @@ class BatchPlan:
         check(lib.ts_batch_run(self._h, n, segs, qps, _current_stream(stream)))
 
     def wait(self) -> dict:
+        """Wait for the last run: {"rows", "nreq", "overflow", "stats"} (the statistics dict is
+        built when first read)."""
         lib = _lib.load()
         st = _lib.ts_batch_status()
         check(lib.ts_batch_wait(self._h, ctypes.byref(st)))
         self._keep = None
         self._last = (int(st.nreq), int(st.rows))
-        return {"rows": int(st.rows), "nreq": int(st.nreq), "overflow": bool(st.overflow),
-                "stats": st.stats.as_dict()}
+        return _Outcome(st)
 
     def request_rows(self, r):
         lib = _lib.load()
