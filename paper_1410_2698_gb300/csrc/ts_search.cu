@@ -806,13 +806,14 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
 
     // tiles are taken from a device counter; the next index and its descriptor are fetched
     // while a tile is swept
-    uint64_t t = 0;
-    if (lane == 0) t = atomicAdd(&B.counters[PASS], 1u);
-    t = __shfl_sync(FULL, t, 0);
+    // (each warp's first tile is its index in the grid, so the counter only hands out the rest:
+    // no burst of same-address atomics when every warp starts at once)
+    const uint32_t nwarps = gridDim.x * PK_WARPS;
+    uint64_t t = (uint64_t)blockIdx.x * PK_WARPS + wid;
     uint4 D = t < ntiles ? B.tdesc[t] : make_uint4(0u, 0u, 0u, 0u);
     while (!abort && t < ntiles) {
         uint64_t t_next = 0;
-        if (lane == 0) t_next = atomicAdd(&B.counters[PASS], 1u);
+        if (lane == 0) t_next = nwarps + (uint64_t)atomicAdd(&B.counters[PASS], 1u);
         if (PASS == PASS_WRITE && B.tile_hits[t] == 0) {  // no rows in this tile
             t = __shfl_sync(FULL, t_next, 0);
             D = t < ntiles ? B.tdesc[t] : make_uint4(0u, 0u, 0u, 0u);
