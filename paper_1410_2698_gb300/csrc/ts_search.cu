@@ -647,7 +647,7 @@ struct __align__(16) WarpSmem {
     unsigned long long bar[PK_STAGES];
     unsigned long long mbar;  // members + chunk boxes
     // counts of the count pass: chunks, bitmask chunks, sparse member visits, survivors (then,
-    // at the end, the warp's tests, FP64 tests and hits)
+    // at the end, the warp's tests, FP64 tests and hits; the last slot pads to 64 bytes)
     unsigned long long sweep[8];
 };
 
@@ -682,7 +682,8 @@ __device__ __noinline__ bool exact_test(const QueryD *qp, const SegD *ep, bool i
 }
 
 // Persistent pair kernel. Warps take tiles (a group of up to 32 query units and up to `tile`
-// consecutive entries of one sorted array) from a device counter. Entry records stream through
+// consecutive entries of one sorted array): the first by their index in the grid, the rest from
+// a device counter. Entry records stream through
 // a ring of PK_STAGES shared-memory buffers filled by 1-D bulk copies. The conservative FP32
 // filters pick the candidates of the exact FP64 test; those wait in a per-warp queue that is
 // carried across tiles and drained 32 at a time, so that the FP64 instructions run on full warps.
