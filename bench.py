@@ -38,7 +38,7 @@ INTERVAL_FLOPS = 10        # FP64 flops per hit for the roots (sqrt, 2 div, clam
 # dram__bytes_write.sum from one ncu capture of this bench on a GB300, valid while the kernel's
 # sources hash to `sources` (otherwise the line reports null)
 PAIR_TRAFFIC = {
-    "random-walk-1m": {"bytes_per_launch": 22368128, "sources": "2c9560f8f3e86e24",
+    "random-walk-1m": {"bytes_per_launch": 19615381, "sources": "a11f1236f22bee68",
                        "capture": "profiles/k_pair_random-walk-1m_batched.md"},
 }
 PAIR_SOURCES = ("ts_search.cuh", "ts_internal.cuh", "ts_device.cuh")
