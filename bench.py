@@ -185,13 +185,13 @@ def measured_peaks():
 
 def roofline(tot, pair_ms, peaks=None):
     """Roofline of the pair kernel (count + write passes): the slower of the FP32 filter and the
-    FP64 exact test at their pipes' peaks (measured on this GPU when `peaks` is given, else
-    derived / nominal); algorithmic work counted once. Beside it, for context, the per-candidate
-    FP64 roofline (every candidate charged a full FP64 test and its 68 bytes), which the FP32
-    filter lets the kernel exceed."""
+    FP64 exact test at their pipes' peaks, derived from the unit counts and the maximum clock
+    (FP32: 152 SMs x 128 lanes x 2 flops x 2.07 GHz; FP64: GB300's nominal rate); algorithmic
+    work counted once. The same pipes' rates measured on this GPU by FMA loops (`peaks`) are
+    reported beside them. Also for context, the per-candidate FP64 roofline (every candidate
+    charged a full FP64 test and its 68 bytes), which the FP32 filter lets the kernel exceed."""
     t_s = pair_ms / 1e3
-    p32 = peaks["fp32_tflops"] if peaks else FP32_PEAK_TFLOPS
-    p64 = peaks["fp64_tflops"] if peaks else FP64_PEAK_TFLOPS
+    p32, p64 = FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS
     f32 = tot["n_tests"] * PREFILTER_FLOPS
     f64 = tot["n_exact"] * EXACT_FLOPS + tot["n_hits"] * INTERVAL_FLOPS
     lb32 = f32 / (p32 * 1e12)
@@ -199,25 +199,32 @@ def roofline(tot, pair_ms, peaks=None):
     if lb32 >= lb64:
         ach = f32 / t_s / 1e12 if t_s > 0 else 0.0
         peak = p32
+        meas = peaks["fp32_tflops"] if peaks else None
         pipe = "fp32 (conservative filter)"
     else:
         ach = f64 / t_s / 1e12 if t_s > 0 else 0.0
         peak = p64
+        meas = peaks["fp64_tflops"] if peaks else None
         pipe = "fp64 (exact test)"
     hbm = measured_peaks().get("hbm_gbs")
     tests_s = tot["n_tests"] / t_s if t_s > 0 else 0.0
     bound = min(p64 * 1e12 / 50.0, (hbm or 6771.1) * 1e9 / 68.0)
-    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak if peak else None, "traffic": None,
-            "kernel": "k_pair (count + write passes)", "pipe": pipe,
-            "peak_source": ("measured on this GPU: FMA loops (ts_measure_alu_peaks), "
-                            f"FP32 {p32:.1f}, FP64 {p64:.3f} TFLOP/s") if peaks else
-                           "derived: 152 SMs x lanes x 2.07 GHz (FP32), GB300 nominal (FP64)",
-            "per_candidate_fp64_roofline": {
-                "tests_per_s": tests_s, "bound_tests_per_s": bound,
-                "ratio": tests_s / bound if bound else None,
-                "note": "every candidate charged 50 FP64 flops and 68 B; the FP32 filter decides "
-                        "almost all candidates without the FP64 pipe"}}
+    out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+           "frac": ach / peak if peak else None, "traffic": None,
+           "kernel": "k_pair (count + write passes)", "pipe": pipe,
+           "peak_source": "derived from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 x "
+                          "2.07 GHz = 80.5 TFLOP/s (FP32); GB300 nominal 1.25 TFLOP/s (FP64)",
+           "per_candidate_fp64_roofline": {
+               "tests_per_s": tests_s, "bound_tests_per_s": bound,
+               "ratio": tests_s / bound if bound else None,
+               "note": "every candidate charged 50 FP64 flops and 68 B; the FP32 filter decides "
+                       "almost all candidates without the FP64 pipe"}}
+    if meas:
+        out["measured_peak"] = meas
+        out["frac_of_measured"] = ach / meas
+        out["measured_peak_source"] = ("FMA loops over every SM on this GPU "
+                                       "(ts_measure_alu_peaks), CUDA events")
+    return out
 
 
 def _timed(args, stream, flush, step, steps=None):
