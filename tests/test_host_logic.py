@@ -1,0 +1,62 @@
+"""Host-side logic that needs no GPU: request marshalling for batch plans, the benchmark's
+roofline arithmetic and the gating of its DRAM-traffic figure on the pair kernel's sources."""
+import ctypes
+import os
+import sys
+
+import numpy as np
+
+from paper_1410_2698_gb300 import api, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_prepared_requests_point_at_the_callers_columns():
+    w = workloads.tiny()
+    q = w.queries
+    reqs = [(q, 1.0, 0.0, 70.0), (q, 5.0, 3.0, 60.0, 1000)]
+    prep = api.prepare_requests(reqs)
+    assert prep.n == 2
+    for r, (_, d, ts, te, *mr) in enumerate(reqs):
+        s, p = prep.segs[r], prep.qps[r]
+        assert s.n == q.n and s.on_host == 1
+        # the marshalled columns are the caller's arrays, not copies
+        assert ctypes.cast(s.x0, ctypes.c_void_p).value == q.x0.ctypes.data
+        assert ctypes.cast(s.t1, ctypes.c_void_p).value == q.t1.ctypes.data
+        assert (p.d, p.t_start, p.t_end) == (d, ts, te)
+        assert p.max_results == (mr[0] if mr else 0)
+
+
+def test_roofline_picks_the_slower_pipe_against_derived_peaks():
+    # FP32-dominated: 1e9 candidates x 20 flops in 1 ms = 20 TFLOP/s of the FP32 bound
+    r = bench.roofline({"n_tests": 1e9, "n_exact": 1e3, "n_hits": 1e2}, 1.0,
+                       {"fp32_tflops": 78.5, "fp64_tflops": 1.057})
+    assert r["bound"] == "alu" and r["pipe"].startswith("fp32")
+    assert abs(r["achieved"] - 20.0) < 1e-9
+    assert abs(r["peak"] - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+    assert abs(r["frac"] - 20.0 / r["peak"]) < 1e-12
+    assert abs(r["frac_of_measured"] - 20.0 / 78.5) < 1e-12
+    # FP64-dominated: 1e9 exact tests x 41 + 5e8 hits x 10 flops in 100 ms
+    r = bench.roofline({"n_tests": 1e9, "n_exact": 1e9, "n_hits": 5e8}, 100.0, None)
+    assert r["pipe"].startswith("fp64") and r["peak"] == 1.25
+    assert abs(r["achieved"] - (41e9 + 5e9) / 0.1 / 1e12) < 1e-9
+    assert "measured_peak" not in r
+
+
+def test_traffic_figure_is_keyed_to_the_pair_kernel_sources(tmp_path):
+    csrc = os.path.join(ROOT, "paper_1410_2698_gb300", "csrc")
+    h = bench.pair_source_hash()
+    assert h == bench.pair_source_hash(csrc) and len(h) == 16
+    # a change inside the pair kernel's section changes the hash; one outside it does not
+    for f in bench.PAIR_SOURCES + ("ts_search.cu",):
+        with open(os.path.join(csrc, f), "rb") as src:
+            (tmp_path / f).write_bytes(src.read())
+    text = (tmp_path / "ts_search.cu").read_bytes()
+    a = text.index(b"\n// pair kernel\n")
+    (tmp_path / "ts_search.cu").write_bytes(text[:a] + b"\n// (outside)\n" + text[a:])
+    assert bench.pair_source_hash(str(tmp_path)) == h
+    b = text.index(b"__global__", a)
+    (tmp_path / "ts_search.cu").write_bytes(text[:b] + b"/* inside */ " + text[b:])
+    assert bench.pair_source_hash(str(tmp_path)) != h
