@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--tile", type=int, default=0, help="records per work tile (0 = default)")
     ap.add_argument("--pair-blocks", type=int, default=0, help="pair kernel blocks (0 = all)")
+    ap.add_argument("--t-bins", type=int, default=0,
+                    help="temporal bins of the temporal and spatiotemporal indexes when not "
+                         "autotuned (0 = the index's default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="default index parameters, tiles and pair grid instead of the "
                          "autotuner's (which times the batched form before the timed region)")
@@ -282,8 +285,13 @@ def run_gpu(args):
         treqs = [(w.queries, d, w.t_start, w.t_end) for d in w.distances]
         for k in kinds:
             tuned[k] = autotune.tune(w.db, treqs, k, repeats=10)
-    indexes = {k: api.ts_build_index(w.db, kind=k, **(tuned[k]["index"] if k in tuned else {}))
-               for k in kinds}
+    def index_params(k):
+        if k in tuned:
+            return tuned[k]["index"]
+        return {"t_bins": args.t_bins} if args.t_bins and k in ("temporal",
+                                                                  "spatiotemporal") else {}
+
+    indexes = {k: api.ts_build_index(w.db, kind=k, **index_params(k)) for k in kinds}
     qdev = {f: torch.from_numpy(getattr(w.queries, f)).to(dev) for f in Segments.FIELDS}
     torch.cuda.synchronize()
     peaks = api.ts_measure_alu_peaks()  # roofline denominators, measured before the timed region
