@@ -519,6 +519,9 @@ def run_gpu(args):
                    "l2": "flushed (256 MB write) before every timed step",
                    "tile_records": args.tile or 256, "pair_blocks": args.pair_blocks or "all"},
         "tests_per_s": btot["n_tests"] * world / (batch_total / 1e3),
+        # every clipped query segment against every database segment, per second (what an
+        # all-pairs search would have to evaluate; a label, not a count of work done)
+        "brute_equivalent_pairs_per_s": btot["n_qsegs"] * w.db.n * world / (batch_total / 1e3),
         "hits_per_step": btot["n_hits"] // max(args.steps, 1),
         "gpu_launches": int(l2 - l1),
         "clocks": clk,
