@@ -257,7 +257,7 @@ void form_batch(Server *s, std::vector<SrvReq *> &batch)
     }
 }
 
-ts_status launch_slot(Server *s, Slot &sl)
+ts_status launch_slot(Slot &sl)
 {
     std::vector<ts_segments> segs(sl.batch.size());
     std::vector<ts_query_params> qps(sl.batch.size());
@@ -317,7 +317,7 @@ void loop(Server *s)
                 q->batch_requests = (uint32_t)sl.batch.size();
             }
             lk.unlock();
-            ts_status st = launch_slot(s, sl);
+            ts_status st = launch_slot(sl);
             lk.lock();
             if (st != TS_OK) {
                 const char *msg = last_error();
