@@ -60,3 +60,27 @@ def test_shard_ranges_cover_without_splitting_trajectories():
             assert b == c
         for a, b in rng:
             assert a in set(first.tolist()) | {50}
+
+
+def _timing_rank(rank, world, port, out_dir):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch
+    import torch.distributed as dist
+
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    # every rank times its own share; the job's time is the slowest rank's
+    t = bench._max_over_ranks(10.0 + rank, world, torch.device("cpu"))
+    with open(os.path.join(out_dir, f"t{rank}"), "w") as f:
+        f.write(repr(t))
+    dist.destroy_process_group()
+
+
+def test_bench_takes_the_slowest_rank_time(tmp_path):
+    port = _free_port()
+    mp.start_processes(_timing_rank, args=(3, port, str(tmp_path)), nprocs=3, join=True,
+                       start_method="spawn")
+    for r in range(3):
+        assert float((tmp_path / f"t{r}").read_text()) == 12.0
