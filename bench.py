@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import itertools
 import json
 import math
 import os
@@ -349,37 +350,53 @@ def run_gpu(args):
     alone = []
     plans = {}
     step_pair_blocks = None
-    if not serial and args.autotune and not args.pair_blocks:
+    order = list(kinds)  # the order the plans of a step are launched in
+
+    def time_step(trial, seq, reps=20):
+        for _ in range(8):  # warm-up (graph capture), then the timed trials
+            for k in seq:
+                trial[k].run(preq, stream=0)
+            for k in seq:
+                trial[k].wait()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for k in seq:
+                trial[k].run(preq, stream=0)
+            for k in seq:
+                trial[k].wait()
+        return time.perf_counter() - t0
+
+    if not serial and args.autotune:
         # the plans of a step overlap on their own streams, and a persistent pair kernel holds
-        # the SMs it runs on: the pair grid is tuned on the overlapped step itself (all resident
-        # blocks, or 1.75 to 1 block per SM), outside the timed region
+        # the SMs it runs on: the pair grid (all resident blocks, or 1.75 to 1 block per SM) and
+        # then the order in which the plans are launched are tuned on the overlapped step
+        # itself, outside the timed region
+        if not args.pair_blocks:
+            best = None
+            for pb in (0, 266, 228, 190, 152):
+                trial = {k: make_plan(k, True, pb) for k in kinds}
+                dt = time_step(trial, kinds)
+                for pl in trial.values():
+                    pl.free()
+                if best is None or dt < best[1]:
+                    best = (pb, dt)
+            step_pair_blocks = best[0]
+        trial = {k: make_plan(k, True, step_pair_blocks) for k in kinds}
         best = None
-        for pb in (0, 266, 228, 190, 152):
-            trial = {k: make_plan(k, True, pb) for k in kinds}
-            for _ in range(8):  # warm-up (graph capture), then the timed trials
-                for k in kinds:
-                    trial[k].run(preq, stream=0)
-                for k in kinds:
-                    trial[k].wait()
-            t0 = time.perf_counter()
-            for _ in range(20):
-                for k in kinds:
-                    trial[k].run(preq, stream=0)
-                for k in kinds:
-                    trial[k].wait()
-            dt = time.perf_counter() - t0
-            for pl in trial.values():
-                pl.free()
+        for seq in itertools.permutations(kinds):
+            dt = time_step(trial, list(seq))
             if best is None or dt < best[1]:
-                best = (pb, dt)
-        step_pair_blocks = best[0]
+                best = (list(seq), dt)
+        order = best[0]
+        for pl in trial.values():
+            pl.free()
     if not serial:
         plans = {k: make_plan(k, True, step_pair_blocks) for k in kinds}
 
         def batched_step(collect=None):
-            for k in kinds:
+            for k in order:
                 plans[k].run(preq, stream=0)  # each plan on its own stream: the plans overlap
-            for k in kinds:
+            for k in order:
                 st = plans[k].wait()
                 if st["overflow"]:
                     raise RuntimeError(f"batch plan overflow for {k}")
@@ -535,6 +552,8 @@ def run_gpu(args):
         "breakdown": breakdown,
     }
     line["config"]["plans"] = "one at a time" if serial else "resident together, overlapped"
+    if not serial:
+        line["config"]["launch_order"] = order
     if tuned:
         line["config"]["autotuned"] = {k: {"index": v["index"], "tile_records": v["tile_records"],
                                            "pair_blocks": args.pair_blocks or (
@@ -546,7 +565,7 @@ def run_gpu(args):
         if serial:
             line["e2e"] = run_e2e(args, api, w, None, kinds, make_plan, most)
         else:
-            line["e2e"] = run_e2e(args, api, w, plans, kinds, max_rows=most)
+            line["e2e"] = run_e2e(args, api, w, plans, order, max_rows=most)
     if not args.no_served and rank == 0:
         sk = args.served_index
         sidx = indexes[sk] if sk in indexes else api.ts_build_index(w.db, kind=sk)
