@@ -13,7 +13,6 @@ from __future__ import annotations
 
 import argparse
 import hashlib
-import itertools
 import json
 import math
 import os
@@ -351,45 +350,14 @@ def run_gpu(args):
     plans = {}
     step_pair_blocks = None
     order = list(kinds)  # the order the plans of a step are launched in
-
-    def time_step(trial, seq, reps=20):
-        for _ in range(8):  # warm-up (graph capture), then the timed trials
-            for k in seq:
-                trial[k].run(preq, stream=0)
-            for k in seq:
-                trial[k].wait()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            for k in seq:
-                trial[k].run(preq, stream=0)
-            for k in seq:
-                trial[k].wait()
-        return time.perf_counter() - t0
-
     if not serial and args.autotune:
-        # the plans of a step overlap on their own streams, and a persistent pair kernel holds
-        # the SMs it runs on: the pair grid (all resident blocks, or 1.75 to 1 block per SM) and
-        # then the order in which the plans are launched are tuned on the overlapped step
-        # itself, outside the timed region
-        if not args.pair_blocks:
-            best = None
-            for pb in (0, 266, 228, 190, 152):
-                trial = {k: make_plan(k, True, pb) for k in kinds}
-                dt = time_step(trial, kinds)
-                for pl in trial.values():
-                    pl.free()
-                if best is None or dt < best[1]:
-                    best = (pb, dt)
-            step_pair_blocks = best[0]
-        trial = {k: make_plan(k, True, step_pair_blocks) for k in kinds}
-        best = None
-        for seq in itertools.permutations(kinds):
-            dt = time_step(trial, list(seq))
-            if best is None or dt < best[1]:
-                best = (list(seq), dt)
-        order = best[0]
-        for pl in trial.values():
-            pl.free()
+        # the plans of a step overlap on their own streams: the pair grid they share and the
+        # order they are launched in are tuned on the overlapped step itself, outside the timed
+        # region
+        from paper_1410_2698_gb300 import autotune
+        step_pair_blocks, order = autotune.tune_overlapped(
+            lambda pb: {k: make_plan(k, True, pb) for k in kinds}, kinds, preq,
+            tune_grid=not args.pair_blocks)
     if not serial:
         plans = {k: make_plan(k, True, step_pair_blocks) for k in kinds}
 

@@ -176,6 +176,57 @@ STUDY = {
 }
 
 
+def time_overlapped(plans, requests, order, warmup=8, reps=20):
+    """Wall time of `reps` steps that launch every plan (each on its own stream) in `order`, then
+    wait for each; `warmup` untimed steps first (the first also captures the plans' graphs)."""
+    for _ in range(warmup):
+        for k in order:
+            plans[k].run(requests, stream=0)
+        for k in order:
+            plans[k].wait()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for k in order:
+            plans[k].run(requests, stream=0)
+        for k in order:
+            plans[k].wait()
+    return time.perf_counter() - t0
+
+
+def tune_overlapped(make_plans, kinds, requests, grids=(0, 266, 228, 190, 152), tune_grid=True,
+                    timer=time_overlapped):
+    """Tune a step that runs several plans at once (one per kind, overlapping on their streams):
+    first the persistent pair kernel's grid shared by the plans (`grids`, 0 = all resident
+    blocks; a pair kernel holds the SMs it runs on, so a smaller grid leaves room for the other
+    plans' kernels), then the order in which the plans are launched. make_plans(pair_blocks)
+    returns {kind: plan}; the plans it returns are freed here. Returns (pair_blocks, order)."""
+    import itertools
+    pair_blocks = None
+    if tune_grid:
+        best = None
+        for pb in grids:
+            plans = make_plans(pb)
+            try:
+                dt = timer(plans, requests, list(kinds))
+            finally:
+                for pl in plans.values():
+                    pl.free()
+            if best is None or dt < best[1]:
+                best = (pb, dt)
+        pair_blocks = best[0]
+    plans = make_plans(pair_blocks)
+    try:
+        best = None
+        for seq in itertools.permutations(kinds):
+            dt = timer(plans, requests, list(seq))
+            if best is None or dt < best[1]:
+                best = (list(seq), dt)
+    finally:
+        for pl in plans.values():
+            pl.free()
+    return pair_blocks, best[0]
+
+
 def study(db, queries, distances, t_start, t_end, kinds=("temporal", "spatiotemporal", "spatial"),
           repeats=3):
     """Response of the search to the index's bin granularity (the temporal bins m, the subbins v,

@@ -80,3 +80,41 @@ def test_reference_arm_prints_the_contract_line():
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert "workload" in line["config"]
+
+
+def test_overlapped_step_tuning_picks_the_fastest_grid_then_order():
+    from paper_1410_2698_gb300 import autotune
+
+    class FakePlan:
+        live = 0
+
+        def __init__(self, pb):
+            self.pb = pb
+            FakePlan.live += 1
+
+        def free(self):
+            FakePlan.live -= 1
+
+    kinds = ["spatiotemporal", "temporal", "spatial"]
+    grid_cost = {0: 5.0, 266: 3.0, 228: 2.0, 190: 4.0, 152: 6.0}
+    seen = []
+
+    def timer(plans, requests, order):
+        pb = next(iter(plans.values())).pb
+        seen.append((pb, tuple(order)))
+        # the grid is timed in the given order; then the order matters (temporal first best)
+        return grid_cost[pb] + (0.0 if order[0] == "temporal" else 1.0) + 0.1 * order.index(
+            "spatial")
+
+    pb, order = autotune.tune_overlapped(lambda pb: {k: FakePlan(pb) for k in kinds}, kinds,
+                                         None, timer=timer)
+    assert pb == 228
+    assert order[0] == "temporal" and order == ["temporal", "spatial", "spatiotemporal"]
+    assert FakePlan.live == 0  # every plan made for a trial was freed
+    assert len(seen) == 5 + 6
+    # with the grid given, only the order is tuned (plans made with pair_blocks None)
+    seen.clear()
+    pb, order = autotune.tune_overlapped(lambda pb: {k: FakePlan(228 if pb is None else pb)
+                                                      for k in kinds}, kinds, None,
+                                         tune_grid=False, timer=timer)
+    assert pb is None and len(seen) == 6 and order[0] == "temporal"
