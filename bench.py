@@ -1,10 +1,12 @@
 """Benchmark of the GB300 trajectory distance threshold search.
 
-Workload (default): the Random-walk 1M configuration -- 2,500 random-walk trajectories x 401
-samples (1,000,000 database segments), 25 query trajectories (10,000 query segments), full time
-span, d in {1, 5, 10, 25}. One step = one query batch searched at every d with every index
-(spatiotemporal, temporal, spatial when available): the whole search path (query preparation,
-schedule, grouping, pair kernel count pass, scan, write pass) per search, inputs resident in HBM.
+Workload (default): the merger-like configuration -- two Plummer spheres of 50,000 particles
+each, 201 samples (20,000,000 database segments, 1.28 GB of FP64 segments), 2,000 query
+trajectories from the cluster cores (400,000 query segments), full time span, d in {1, 5}. One
+step = the query set searched at every d with every index (spatiotemporal, temporal, spatial): the
+whole search path (query preparation, schedule, grouping, pair kernel count pass, scan, row
+placement / write pass) per search, inputs resident in HBM. Other workloads: --workload
+random-walk-1m | dense | tiny | merger-like-2m.
 
 Prints ONE JSON line (rank 0). With --impl reference the CPU oracle is timed instead on the host
 cores, on a bounded sample of the same workload.
@@ -16,6 +18,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -28,19 +31,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "seg-pair tests/s & query segs/s, plain vs batched/served; p50/p99 latency"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
-FP64_PEAK_TFLOPS = 1.25                              # GB300 FP64 (nominal)
-PREFILTER_FLOPS = 20       # FP32 flops per candidate test (6 sub, 6 max, 1 mul + 2 fma, 3 cmp)
-EXACT_FLOPS = 41           # FP64 flops per exact test (window, positions, a, b, c, decision)
-INTERVAL_FLOPS = 10        # FP64 flops per hit for the roots (sqrt, 2 div, clamps)
-# DRAM traffic of the pair kernel per launch (count and write passes of the three plans, averaged
-# over the launches of the timed one-plan-at-a-time loop): dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of this bench on a GB300, valid while the kernel's
-# sources hash to `sources` (otherwise the line reports null)
-PAIR_TRAFFIC = {
-    "random-walk-1m": {"bytes_per_launch": 19615381, "sources": "a11f1236f22bee68",
-                       "capture": "profiles/k_pair_random-walk-1m_batched.md"},
-}
+EXACT_FLOPS = 41     # FP64 flops per exact test of the definition (window, positions, a, b, c, decision)
+INTERVAL_FLOPS = 10  # FP64 flops per hit for the roots (sqrt, 2 div, clamps; sqrt and div as 1 each)
+# Per-unit counts of the pair kernel from one ncu capture of the same kernel sources (hash
+# `sources`; a profile of other sources is not used): per exact FP64 test, the FP64-pipe thread
+# instructions (smsp__inst_executed_pipe_fp64.sum x 32 / exact tests: the exact tests run on full
+# warps) at the capture's hits per exact test (`hit_ratio`); per candidate test, the warp
+# instructions issued (smsp__inst_executed.sum / tests); per launch, DRAM bytes
+# (dram__bytes_read.sum + dram__bytes_write.sum) per candidate test.
+PAIR_PROFILE = {}
 PAIR_SOURCES = ("ts_search.cuh", "ts_internal.cuh", "ts_device.cuh")
 
 
@@ -63,10 +62,10 @@ def pair_source_hash(csrc=None):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="random-walk-1m")
+    ap.add_argument("--workload", default="merger-like")
     ap.add_argument("--indexes", default="spatiotemporal,temporal,spatial")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -79,12 +78,18 @@ def parse():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="default index parameters, tiles and pair grid instead of the "
                          "autotuner's (which times the batched form before the timed region)")
+    ap.add_argument("--tune-sample", type=float, default=0.0,
+                    help="fraction of the query trajectories the autotuner times (0 = all, or "
+                         "a tenth on workloads of more than 5M database segments)")
     ap.add_argument("--serial-plans", action="store_true",
                     help="one batch plan at a time (automatic when the plans would not fit)")
     ap.add_argument("--served-index", default="spatiotemporal")
     ap.add_argument("--served-requests", type=int, default=200)
-    ap.add_argument("--served-max-traj", type=int, default=500)
-    ap.add_argument("--served-rho", type=float, default=0.9)
+    ap.add_argument("--served-max-traj", type=int, default=0,
+                    help="largest request, in query trajectories (0 = 5,000 on the merger-like "
+                         "database, 500 otherwise)")
+    ap.add_argument("--served-rho", default="0.5,0.9,1.5",
+                    help="Poisson arrival rates as multiples of the plain request rate")
     ap.add_argument("--served-only", action="store_true",
                     help="only the served form (its own JSON line) on the workload's database")
     ap.add_argument("--study", action="store_true",
@@ -115,7 +120,8 @@ def load_workload(name, rank):
     if name == "dense":
         return workloads.dense()
     if name == "merger-like":
-        return workloads.merger_like()
+        # each rank searches its own draw of core query trajectories (weak scaling)
+        return workloads.merger_like(query_seed_offset=rank)
     if name == "merger-like-2m":  # a tenth of the particles (profiling size)
         return workloads.merger_like(n_per_cluster=5000, n_query_traj=200)
     raise SystemExit(f"unknown workload {name}")
@@ -186,47 +192,82 @@ def measured_peaks():
         return {}
 
 
-def roofline(tot, pair_ms, peaks=None):
-    """Roofline of the pair kernel (count + write passes): the slower of the FP32 filter and the
-    FP64 exact test at their pipes' peaks, derived from the unit counts and the maximum clock
-    (FP32: 152 SMs x 128 lanes x 2 flops x 2.07 GHz; FP64: GB300's nominal rate); algorithmic
-    work counted once. The same pipes' rates measured on this GPU by FMA loops (`peaks`) are
-    reported beside them. Also for context, the per-candidate FP64 roofline (every candidate
-    charged a full FP64 test and its 68 bytes), which the FP32 filter lets the kernel exceed."""
+def device_info(dev):
+    """SM count and maximum SM clock of the device (the derived issue peak's unit counts)."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    mhz = measured_peaks().get("sm_max_mhz")
+    if not mhz:
+        try:
+            out = subprocess.run(["nvidia-smi", f"--id={dev.index or 0}",
+                                  "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                                 capture_output=True, text=True, timeout=10).stdout
+            mhz = float(out.split()[0])
+        except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+            mhz = None
+    return {"sms": int(props.multi_processor_count), "sm_max_mhz": mhz, "name": props.name}
+
+
+def roofline(tot, pair_ms, peaks, workload, dev_info):
+    """Roofline of the pair kernel (its count and write passes, timed by the CUDA events its plans
+    record around them inside the timed step). The kernel's work runs on two pipes: the FP64 pipe
+    (the exact tests; the FP32 filters decide every other candidate) and the issue slots of the SM
+    sub-partitions (the FP32 filters' sweep). For each, achieved = the instructions the kernel
+    issued for this step's work (per-unit counts from the ncu capture of the same sources, times
+    this step's exact tests or candidate tests) / the kernel's time; peak = the FP64 pipe's
+    measured instruction rate (the DFMA loop of ts_measure_alu_peaks: TFLOP/s / 2) or the issue
+    rate derived from the unit counts (SMs x 4 sub-partitions x 1 warp instruction per clock x the
+    maximum SM clock). The bound is the pipe with the larger fraction. Beside it: the algorithmic
+    FP64 flops of the definition (41 per exact test, 10 per hit) against the measured DFMA peak,
+    and HBM bytes from the capture."""
     t_s = pair_ms / 1e3
-    p32, p64 = FP32_PEAK_TFLOPS, FP64_PEAK_TFLOPS
-    f32 = tot["n_tests"] * PREFILTER_FLOPS
-    f64 = tot["n_exact"] * EXACT_FLOPS + tot["n_hits"] * INTERVAL_FLOPS
-    lb32 = f32 / (p32 * 1e12)
-    lb64 = f64 / (p64 * 1e12)
-    if lb32 >= lb64:
-        ach = f32 / t_s / 1e12 if t_s > 0 else 0.0
-        peak = p32
-        meas = peaks["fp32_tflops"] if peaks else None
-        pipe = "fp32 (conservative filter)"
-    else:
-        ach = f64 / t_s / 1e12 if t_s > 0 else 0.0
-        peak = p64
-        meas = peaks["fp64_tflops"] if peaks else None
-        pipe = "fp64 (exact test)"
-    hbm = measured_peaks().get("hbm_gbs")
-    tests_s = tot["n_tests"] / t_s if t_s > 0 else 0.0
-    bound = min(p64 * 1e12 / 50.0, (hbm or 6771.1) * 1e9 / 68.0)
-    out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-           "frac": ach / peak if peak else None, "traffic": None,
-           "kernel": "k_pair (count + write passes)", "pipe": pipe,
-           "peak_source": "derived from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 x "
-                          "2.07 GHz = 80.5 TFLOP/s (FP32); GB300 nominal 1.25 TFLOP/s (FP64)",
-           "per_candidate_fp64_roofline": {
-               "tests_per_s": tests_s, "bound_tests_per_s": bound,
-               "ratio": tests_s / bound if bound else None,
-               "note": "every candidate charged 50 FP64 flops and 68 B; the FP32 filter decides "
-                       "almost all candidates without the FP64 pipe"}}
-    if meas:
-        out["measured_peak"] = meas
-        out["frac_of_measured"] = ach / meas
-        out["measured_peak_source"] = ("FMA loops over every SM on this GPU "
-                                       "(ts_measure_alu_peaks), CUDA events")
+    prof = PAIR_PROFILE.get(workload)
+    cur = pair_source_hash()
+    valid = prof is not None and prof["sources"] == cur
+    fp64_inst_peak = peaks["fp64_tflops"] * 1e12 / 2.0
+    mhz = dev_info.get("sm_max_mhz") or 0.0
+    issue_peak = dev_info["sms"] * 4 * mhz * 1e6
+    alg = (tot["n_exact"] * EXACT_FLOPS + tot["n_hits"] * INTERVAL_FLOPS)
+    out = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+           "traffic": None, "kernel": "k_pair (count + write passes)",
+           "pair_ms_per_step": pair_ms,
+           "work_per_step": {"candidate_tests": tot["n_tests"], "exact_tests": tot["n_exact"],
+                             "hits": tot["n_hits"]},
+           "algorithmic_fp64": {
+               "achieved_tflops": alg / t_s / 1e12 if t_s > 0 else None,
+               "peak_tflops": peaks["fp64_tflops"],
+               "frac": alg / t_s / 1e12 / peaks["fp64_tflops"] if t_s > 0 else None,
+               "note": "41 FP64 flops per exact test and 10 per hit (sqrt and division one "
+                       "flop each) against the measured DFMA peak (an FMA two flops)"},
+           "profile": prof["capture"] if valid else None,
+           "profile_sources": cur}
+    if not valid or t_s <= 0 or not mhz:
+        out["note"] = ("no ncu capture of the current pair-kernel sources for this workload: "
+                       "the pipe fractions are not computed")
+        return out
+    fp64 = prof["fp64_inst_per_exact"] * tot["n_exact"] / t_s
+    issue = prof["warp_inst_per_test"] * tot["n_tests"] / t_s
+    pipes = {
+        "fp64": {"achieved": fp64 / 1e9, "peak": fp64_inst_peak / 1e9,
+                 "frac": fp64 / fp64_inst_peak, "unit": "G FP64 thread-inst/s",
+                 "peak_source": "measured: DFMA loop over every SM (ts_measure_alu_peaks), "
+                                "TFLOP/s / 2"},
+        "issue": {"achieved": issue / 1e9, "peak": issue_peak / 1e9,
+                  "frac": issue / issue_peak, "unit": "G warp-inst/s",
+                  "peak_source": f"derived: {dev_info['sms']} SMs x 4 sub-partitions x 1 warp "
+                                 f"instruction per clock x {mhz:g} MHz"}}
+    name = max(pipes, key=lambda k: pipes[k]["frac"])
+    top = pipes[name]
+    out.update({"achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+                "frac": top["frac"], "pipe": name, "peak_source": top["peak_source"],
+                "pipes": pipes,
+                "hit_ratio": tot["n_hits"] / max(tot["n_exact"], 1),
+                "profile_hit_ratio": prof.get("hit_ratio")})
+    if prof.get("dram_bytes_per_test") is not None:
+        launches = max(tot.get("launches", 1), 1)
+        out["traffic"] = prof["dram_bytes_per_test"] * tot["n_tests"] / launches
+        out["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled "
+                               "from the capture by the candidate tests of this step's launches")
     return out
 
 
@@ -278,13 +319,24 @@ def run_gpu(args):
     w = load_workload(args.workload, rank)
     kinds = [k for k in args.indexes.split(",") if k]
     tuned = {}
+    tune_note = None
     if args.autotune:
         # the autotuner times the batched form on this workload's requests (outside the timed
-        # region) and caches its choice per workload and GPU
+        # region) and caches its choice per workload and GPU; on a large database it times a
+        # sample of the query trajectories (the choice is per database and index)
         from paper_1410_2698_gb300 import autotune
-        treqs = [(w.queries, d, w.t_start, w.t_end) for d in w.distances]
+        frac = args.tune_sample or (0.1 if w.db.n > 5_000_000 else 1.0)
+        tq = w.queries
+        if frac < 1.0:
+            n_traj = len(w.query_traj_ids)
+            per = w.queries.n // n_traj
+            keep = max(1, int(round(frac * n_traj)))
+            tq = w.queries.take(np.arange(keep * per))
+            tune_note = f"timed on {keep} of {n_traj} query trajectories"
+        treqs = [(tq, d, w.t_start, w.t_end) for d in w.distances]
+        reps = 10 if frac >= 1.0 else 3
         for k in kinds:
-            tuned[k] = autotune.tune(w.db, treqs, k, repeats=10)
+            tuned[k] = autotune.tune(w.db, treqs, k, repeats=reps)
     def index_params(k):
         if k in tuned:
             return tuned[k]["index"]
@@ -295,6 +347,7 @@ def run_gpu(args):
     qdev = {f: torch.from_numpy(getattr(w.queries, f)).to(dev) for f in Segments.FIELDS}
     torch.cuda.synchronize()
     peaks = api.ts_measure_alu_peaks()  # roofline denominators, measured before the timed region
+    dinfo = device_info(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
     stream = torch.cuda.current_stream()
 
@@ -473,36 +526,39 @@ def run_gpu(args):
     for e in per_index.values():
         for key in e:
             e[key] = e[key] / n_alone
-    # roofline of the dominant kernel (the batched pair kernel, count + write passes, timed by
-    # CUDA events the plan records around the passes on its stream, one plan at a time)
-    if apair_ms > 0:
-        roof = roofline(atot, apair_ms, peaks)
-        roof["timed_form"] = "batched, one plan at a time (separate loop of the same plans)"
-        roof["pair_kernel_share"] = apair_ms / sum(alone_ms) if alone_ms else None
-        roof["ms_per_step_one_at_a_time"] = sum(alone_ms) / n_alone
-        roof["per_index"] = per_index
+    # roofline of the dominant kernel: the batched pair kernel (count + write passes), timed by
+    # the CUDA events each plan records around its passes on its stream. With the plans run one
+    # at a time these are the timed headline step's own events; with overlapped plans (where a
+    # plan's events also span the other plans' kernels) a loop of the same plans one at a time.
+    step_tot = {k: v / n_alone for k, v in atot.items()}  # per step
+    step_tot["launches"] = 2 * len(kinds)  # count + write pass of every plan
+    roof = roofline(step_tot, apair_ms / n_alone, peaks, w.name, dinfo)
+    if serial:
+        roof["timed_form"] = ("batched, the timed headline step itself (plans one at a time; "
+                              "CUDA events of each plan around its pair-kernel passes)")
     else:
-        roof = roofline(tot, pair_ms, peaks)
-        roof["timed_form"] = "plain"
-    cap = PAIR_TRAFFIC.get(w.name)
-    if cap and cap["sources"] == pair_source_hash():
-        roof["traffic"] = cap["bytes_per_launch"]
-        roof["traffic_capture"] = cap["capture"]
-    else:
-        roof["traffic_capture"] = "none for the current kernel sources"
+        roof["timed_form"] = "batched, one plan at a time (a loop of the headline step's plans)"
+    roof["pair_kernel_share"] = apair_ms / sum(alone_ms) if alone_ms else None
+    roof["per_index"] = per_index
     # whole-job aggregates (every rank processes the same amount of work)
     value = btot["n_qsegs"] * world / (batch_total / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "query segs/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded random walks; stand-in for the paper's Random-1M)",
+        "data": "synthetic: " + STAND_IN.get(w.name.split("-")[0], "seeded trajectories"),
         "config": {"workload": f"{w.name}: {w.db.n} db segments, {w.queries.n} query segments, "
                                f"d in {list(w.distances)}, indexes {kinds}",
                    "form": "batched: per index one reusable plan replayed as a CUDA graph, the "
                            "distances are the requests of one batch",
                    "l2": "flushed (256 MB write) before every timed step",
-                   "tile_records": args.tile or 256, "pair_blocks": args.pair_blocks or "all"},
+                   "tile_records": {k: (tuned[k]["tile_records"] if k in tuned else
+                                        (args.tile or 256)) for k in kinds},
+                   "pair_blocks": {k: (step_pair_blocks if step_pair_blocks is not None else
+                                       (args.pair_blocks or (tuned[k]["pair_blocks"]
+                                                             if k in tuned else 0)))
+                                   or "all resident" for k in kinds},
+                   "gpu": f"{dinfo['name']}, {dinfo['sms']} SMs"},
         "tests_per_s": btot["n_tests"] * world / (batch_total / 1e3),
         # every clipped query segment against every database segment, per second (what an
         # all-pairs search would have to evaluate; a label, not a count of work done)
@@ -522,12 +578,13 @@ def run_gpu(args):
     line["config"]["plans"] = "one at a time" if serial else "resident together, overlapped"
     if not serial:
         line["config"]["launch_order"] = order
+    line["config"]["index_params"] = {k: _index_params(indexes[k]) for k in kinds}
     if tuned:
         line["config"]["autotuned"] = {k: {"index": v["index"], "tile_records": v["tile_records"],
-                                           "pair_blocks": args.pair_blocks or (
-                                               v["pair_blocks"] if step_pair_blocks is None
-                                               else step_pair_blocks)}
+                                           "pair_blocks": v["pair_blocks"]}
                                        for k, v in tuned.items()}
+        if tune_note:
+            line["config"]["autotune_sample"] = tune_note
     if not args.no_e2e:
         most = max(rows_per_batch.values()) if rows_per_batch else 0
         if serial:
@@ -537,7 +594,9 @@ def run_gpu(args):
     if not args.no_served and rank == 0:
         sk = args.served_index
         sidx = indexes[sk] if sk in indexes else api.ts_build_index(w.db, kind=sk)
-        line["served"] = run_served(args, api, w, sidx)
+        # the served stream's requests run at the tuned tile size of the served index
+        line["served"] = run_served(args, api, w, sidx,
+                                    tile=tuned[sk]["tile_records"] if sk in tuned else 0)
     if world > 1:
         dist.barrier()
     if rank == 0 and not args.no_cpu:
@@ -550,6 +609,28 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+STAND_IN = {
+    "merger": "two Plummer-sphere clusters on ballistic-plus-jitter paths (stand-in for the "
+              "paper's Merger N-body data)",
+    "random": "seeded random walks (stand-in for the paper's Random-1M)",
+    "dense": "seeded random walks in a box with reflecting walls (stand-in for the paper's "
+             "Random-dense)",
+    "tiny": "seeded random walks (parity case)",
+}
+
+
+def _index_params(index):
+    info = index.info()
+    kind = {0: "brute", 1: "spatial", 2: "temporal", 3: "spatiotemporal"}[int(info["kind"])]
+    if kind == "temporal":
+        return {"t_bins": int(info["t_bins"])}
+    if kind == "spatiotemporal":
+        return {"t_bins": int(info["t_bins"]), "sub_bins": [int(v) for v in info["sub_bins"]]}
+    if kind == "spatial":
+        return {"grid_cells": int(info["grid_cells"])}
+    return {}
 
 
 def _pinned_rows(n):
@@ -624,17 +705,23 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
 
 
-def run_served(args, api, w, index):
+def served_max_traj(args, w):
+    return args.served_max_traj or (5000 if w.name.startswith("merger") else 500)
+
+
+def run_served(args, api, w, index, tile=0):
     """The served form on the resident database: a stream of requests (each a set of query
     trajectory runs with its own interval and d, query arrays on the host) through the request
-    loop, against one plain ts_search per request. Three passes over the same requests:
-    plain (one after another, each synchronous), served at saturation (all submitted at once) and
-    served with Poisson arrivals at rho x the plain request rate. Latency = completion - arrival
-    (the server's clock); every result is released after its count is read."""
+    loop, against one plain ts_search per request. Passes over the same requests: plain (one
+    after another, each synchronous), served at saturation (all submitted at once) and served
+    with Poisson arrivals at rho x the plain request rate for every rho of --served-rho.
+    Latency = completion - arrival (the server's clock); every result is released after its
+    count is read."""
     import threading
     from paper_1410_2698_gb300 import workloads
+    max_traj = served_max_traj(args, w)
     stream = workloads.served_stream(w, n_requests=args.served_requests, rate_per_s=1.0,
-                                     max_traj=args.served_max_traj)
+                                     max_traj=max_traj)
     qsegs = sum(r.queries.n for r in stream)
     max_q = max(r.queries.n for r in stream)
     # plain: one synchronous search per request (after two warm-up searches)
@@ -653,7 +740,8 @@ def run_served(args, api, w, index):
     mu_plain = len(stream) / plain_s
     srv = api.Server(index, max_batch_requests=64, max_batch_queries=max(1 << 20, 2 * max_q),
                      max_batch_rows=max(1 << 25, 2 * max_rows), max_inflight=2, use_graph=True,
-                     linger_us=200)
+                     linger_us=200, tile_records=tile)
+    rhos = [float(x) for x in str(args.served_rho).split(",") if x]
     try:
         def serve(arrivals):
             tickets = [None] * len(stream)
@@ -683,34 +771,61 @@ def run_served(args, api, w, index):
 
         serve(None)  # warm-up: plans captured as graphs
         sat_s, lat_sat, rows_sat, sizes_sat = serve(None)
-        lam = args.served_rho * mu_plain
-        arrivals = [r.arrival_s / lam for r in stream]  # the stream's gaps are at rate 1
-        poi_s, lat_poi, rows_poi, sizes_poi = serve(arrivals)
+        poisson = []
+        for rho in rhos:
+            lam = rho * mu_plain
+            arrivals = [r.arrival_s / lam for r in stream]  # the stream's gaps are at rate 1
+            poi_s, lat_poi, rows_poi, sizes_poi = serve(arrivals)
+            if rows_poi != rows_plain:
+                raise RuntimeError("served and plain forms disagree on the result count")
+            poisson.append({"rho": rho, "arrival_rate_req_s": lam,
+                            "qsegs_per_s": qsegs / poi_s, "p50_ms": _pct(lat_poi, 50),
+                            "p99_ms": _pct(lat_poi, 99),
+                            "mean_batch_requests": float(np.mean(sizes_poi))})
     finally:
         srv.close()
-    if not (rows_plain == rows_sat == rows_poi):
+    if rows_plain != rows_sat:
         raise RuntimeError("served and plain forms disagree on the result count")
     return {
         "index": index_kind_name(index),
         "requests": len(stream), "query_segs": qsegs, "rows": rows_plain,
-        "workload": f"{len(stream)} requests of 1-{args.served_max_traj} query trajectory runs "
-                    f"(log-uniform) of 10-200 segments, interval = the runs' span, d log-uniform "
-                    f"in [0.5, 10]; query arrays on the host",
+        "workload": f"{len(stream)} requests on the resident {w.name} database: 1-{max_traj} "
+                    f"query trajectory runs (log-uniform) of 10-200 segments, interval = the "
+                    f"runs' span, d log-uniform in [0.5, 10]; query arrays on the host",
         "max_request_rows": max_rows,
         "plain": {"qsegs_per_s": qsegs / plain_s, "req_per_s": mu_plain,
-                  "p50_ms": _pct(lat_plain, 50), "p99_ms": _pct(lat_plain, 99)},
+                  "p50_ms": _pct(lat_plain, 50), "p99_ms": _pct(lat_plain, 99),
+                  "form": "one synchronous ts_search per request"},
         "saturated": {"qsegs_per_s": qsegs / sat_s, "req_per_s": len(stream) / sat_s,
                       "p50_ms": _pct(lat_sat, 50), "p99_ms": _pct(lat_sat, 99),
-                      "mean_batch_requests": float(np.mean(sizes_sat))},
-        "poisson": {"rho": args.served_rho, "arrival_rate_req_s": lam,
-                    "qsegs_per_s": qsegs / poi_s, "p50_ms": _pct(lat_poi, 50),
-                    "p99_ms": _pct(lat_poi, 99), "mean_batch_requests": float(np.mean(sizes_poi))},
+                      "mean_batch_requests": float(np.mean(sizes_sat)),
+                      "form": "every request submitted at once"},
+        "poisson": poisson,
     }
 
 
 def index_kind_name(index):
     return {0: "brute", 1: "spatial", 2: "temporal", 3: "spatiotemporal"}.get(
         int(index.info()["kind"]), "?")
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu; /proc/cpuinfo or the platform as fallbacks)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
 
 def cpu_baseline(w, budget_s=8.0):
@@ -738,6 +853,7 @@ def cpu_baseline(w, budget_s=8.0):
             break
         take = min(nq, take * 2)
     out = {"value": qsegs / spent, "unit": "query segs/s", "cores": threads, "kind": "oracle",
+           "cpu": f"{cpu_model()} ({platform.machine()}, {threads} threads)",
            "tests_per_s": tests / spent,
            "sample": f"{rounds} passes over the first up-to-{take} query segments x "
                      f"{len(w.distances)} distances ({spent:.1f} s of CPU time)"}
@@ -765,7 +881,8 @@ def run_reference(args):
     import oracle
     w = load_workload(args.workload, 0)
     threads = os.cpu_count() or 1
-    sample = w.queries.take(np.arange(min(w.queries.n, 800)))
+    # a bounded sample: ~1-2 s of the host's cores per step on every workload
+    sample = w.queries.take(np.arange(min(w.queries.n, 800 if w.db.n <= 2_000_000 else 400)))
     for _ in range(max(args.warmup, 0)):
         oracle.search_count(w.db, sample.take(np.arange(50)), w.t_start, w.t_end, w.distances[0],
                             threads=threads)
@@ -787,7 +904,7 @@ def run_reference(args):
             "config": {"workload": f"{w.name}: {w.db.n} db segments, sample of {sample.n} of "
                                    f"{w.queries.n} query segments, d in {list(w.distances)}"},
             "cpu_baseline": {"value": value, "unit": "query segs/s", "cores": threads,
-                             "kind": "oracle",
+                             "kind": "oracle", "cpu": f"{cpu_model()} ({platform.machine()})",
                              "sample": f"{sample.n} query segments x {len(w.distances)} d per step"},
             "e2e": {"value": value, "unit": "query segs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},

@@ -290,9 +290,16 @@ typedef struct ts_server_params {
     uint32_t tile_records;        /* as in ts_batch_params */
     int32_t use_graph;            /* replay each batch plan as a CUDA graph */
     uint32_t linger_us;           /* how long a partly filled batch waits for more requests */
-    uint32_t reserved;
-    uint64_t scratch_rows;        /* hits a batch's count pass keeps for placement (0 = 2^24);
-                                     a batch with more sweeps its tiles a second time */
+    uint32_t reserved;            /* 0 */
+    uint64_t scratch_rows;        /* hits a batch's count pass keeps for placement (0 = derived
+                                     from the budget: an eighth of it per plan, at 32 B per
+                                     hit); the tiles of hits beyond it are swept a second time */
+    uint64_t mem_budget_bytes;    /* device memory the server may hold: its plans (work buffers
+                                     and scratch) and the rows of results not yet released
+                                     (0 = three quarters of the free device memory at creation).
+                                     A batch whose rows do not fit beside the rows still held
+                                     waits (its plan idle) until results are released; one whose
+                                     rows alone exceed the budget is split */
 } ts_server_params;
 
 typedef struct ts_server ts_server;
@@ -301,7 +308,7 @@ typedef struct ts_server ts_server;
 typedef struct ts_request_timing {
     double submit_us, start_us, done_us;
     uint32_t batch_requests;  /* requests in the batch that served it */
-    uint32_t reserved;
+    uint32_t requeued;        /* times its batch went back to the queue (split, plan growth) */
 } ts_request_timing;
 
 ts_status ts_server_create(const ts_index *idx, const ts_server_params *params,
@@ -317,6 +324,12 @@ ts_status ts_server_submit(ts_server *srv, const ts_segments *q, const ts_query_
  * place; any other status is the request's own outcome and ends its ticket. */
 ts_status ts_server_wait(ts_server *srv, uint64_t ticket, uint32_t timeout_ms, ts_result **out,
                          ts_request_timing *timing);
+
+/* The server's device-memory accounting: its budget (mem_budget_bytes, or the one derived at
+ * creation), the bytes its batch plans hold, and the bytes of result rows not yet released (any
+ * pointer may be NULL). */
+ts_status ts_server_info(ts_server *srv, uint64_t *budget_bytes, uint64_t *plan_bytes,
+                         uint64_t *held_bytes);
 
 /* Cancel a request that has not started; TS_ERR_INVALID_ARG when it already started or ended. */
 ts_status ts_server_cancel(ts_server *srv, uint64_t ticket);
@@ -372,6 +385,25 @@ uint64_t ts_kernel_launches(void);
  * warm-up; ~0.3 s in total). These are the denominators of the pair kernel's roofline (its filter
  * runs on the FP32 pipe, its exact test on the FP64 pipe); the paper has no counterpart. */
 ts_status ts_measure_alu_peaks(double *fp32_tflops, double *fp64_tflops);
+
+/* The exact test's reciprocal and square root beside the CUDA runtime's, for n values x (host
+ * arrays of n doubles each; the call allocates a small device buffer and synchronises the device).
+ * The interval of a hit (the roots s/a and c/s of Sec. 3.1's distance quadratic) uses a hardware
+ * reciprocal or reciprocal-square-root estimate refined by Newton-Raphson steps; this call
+ * evaluates those refinements on the device (rcp_est, sqrt_est; NaN outside their range,
+ * 2^-1000 <= |x| < 2^1000) and the correctly rounded 1/x and sqrt(x) (rcp_ref, sqrt_ref) so a
+ * test can bound their difference. A diagnostic; the paper has no counterpart. */
+ts_status ts_eval_refined_estimates(const double *x, uint64_t n, double *rcp_est,
+                                    double *sqrt_est, double *rcp_ref, double *sqrt_ref);
+
+/* Test hook of the device-side timeout path (the paper has no counterpart). Every wait of the
+ * pair kernel on a bulk copy is bounded (2 s of the GPU's global timer); when one runs out, the
+ * kernel records TS_ERR_TIMEOUT in the search's status word, waits (bounded) for its own copies
+ * still in flight and returns, so the context stays usable. After this call, the count pass of
+ * the next plain search (ts_search or ts_search_points, on any thread) has one warp wait limit_ns
+ * nanoseconds (at most 1e9) on a barrier phase that never completes, then take that path: that
+ * search returns TS_ERR_TIMEOUT. Batch plans and the served loop are not affected. */
+ts_status ts_debug_inject_stall(uint64_t limit_ns);
 
 /* Library version string. */
 const char *ts_version(void);

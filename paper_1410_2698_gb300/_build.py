@@ -3,8 +3,8 @@
 Every translation unit is compiled by one nvcc process (in parallel) for
 ``-gencode arch=compute_103a,code=sm_103a`` and linked into a shared library with the shared CUDA
 runtime. Device code is compiled without FMA contraction (``-fmad=false``) and host code with
-``-ffp-contract=off``: the exact FP64 pair test and the bin/subbin boundaries then round exactly
-as written.
+``-ffp-contract=off``: the bin/subbin boundaries round exactly as written, and the exact FP64 pair
+test fuses exactly the multiply-adds it writes as ``fma()``.
 """
 from __future__ import annotations
 

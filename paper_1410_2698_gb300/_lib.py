@@ -94,13 +94,13 @@ class ts_server_params(ctypes.Structure):
                 ("max_batch_queries", ctypes.c_uint64), ("max_batch_rows", ctypes.c_uint64),
                 ("tile_records", ctypes.c_uint32), ("use_graph", ctypes.c_int32),
                 ("linger_us", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
-                ("scratch_rows", ctypes.c_uint64)]
+                ("scratch_rows", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_uint64)]
 
 
 class ts_request_timing(ctypes.Structure):
     _fields_ = [("submit_us", ctypes.c_double), ("start_us", ctypes.c_double),
                 ("done_us", ctypes.c_double), ("batch_requests", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("requeued", ctypes.c_uint32)]
 
 
 _P = ctypes.c_void_p
@@ -117,6 +117,8 @@ SIGNATURES = {
     "ts_search": (_S, [_P, ctypes.POINTER(ts_segments), ctypes.POINTER(ts_query_params), _P,
                        ctypes.POINTER(_P)]),
     "ts_measure_alu_peaks": (_S, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "ts_eval_refined_estimates": (_S, [_P, ctypes.c_uint64, _P, _P, _P, _P]),
+    "ts_debug_inject_stall": (_S, [ctypes.c_uint64]),
     "ts_search_points": (_S, [_P, _P, _P, _P, ctypes.c_uint64, ctypes.c_int32,
                               ctypes.POINTER(ts_query_params), _P, ctypes.POINTER(_P)]),
     "ts_result_count": (ctypes.c_uint64, [_P]),
@@ -140,6 +142,8 @@ SIGNATURES = {
                            ctypes.POINTER(_P)]),
     "ts_batch_copy_rows": (_S, [_P, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P, _P]),
     "ts_server_create": (_S, [_P, ctypes.POINTER(ts_server_params), ctypes.POINTER(_P)]),
+    "ts_server_info": (_S, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                            ctypes.POINTER(ctypes.c_uint64)]),
     "ts_server_submit": (_S, [_P, ctypes.POINTER(ts_segments), ctypes.POINTER(ts_query_params),
                               ctypes.POINTER(ctypes.c_uint64)]),
     "ts_server_wait": (_S, [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(_P),

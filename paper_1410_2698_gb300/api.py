@@ -307,6 +307,21 @@ def ts_measure_alu_peaks() -> dict:
     return {"fp32_tflops": a.value, "fp64_tflops": b.value}
 
 
+def ts_eval_refined_estimates(x) -> dict:
+    """The exact test's refined 1/x and sqrt(x) and the CUDA runtime's, for a host array x."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = {k: np.empty_like(x) for k in ("rcp_est", "sqrt_est", "rcp_ref", "sqrt_ref")}
+    check(_lib.load().ts_eval_refined_estimates(
+        x.ctypes.data, x.size, *(out[k].ctypes.data for k in ("rcp_est", "sqrt_est", "rcp_ref",
+                                                               "sqrt_ref"))))
+    return out
+
+
+def ts_debug_inject_stall(limit_ns: int) -> None:
+    """Test hook: the next plain search's count pass times out after limit_ns (TS_ERR_TIMEOUT)."""
+    check(_lib.load().ts_debug_inject_stall(int(limit_ns)))
+
+
 def ts_kernel_launches() -> int:
     return int(_lib.load().ts_kernel_launches())
 
@@ -492,12 +507,12 @@ class Server:
 
     def __init__(self, index: Index, max_batch_requests=64, max_batch_queries=1 << 20,
                  max_batch_rows=1 << 26, max_inflight=2, tile_records=0, use_graph=True,
-                 linger_us=200, scratch_rows=0):
+                 linger_us=200, scratch_rows=0, mem_budget_bytes=0):
         lib = _lib.load()
         p = _lib.ts_server_params(int(max_inflight), int(max_batch_requests),
                                   int(max_batch_queries), int(max_batch_rows),
                                   int(tile_records), int(use_graph), int(linger_us), 0,
-                                  int(scratch_rows))
+                                  int(scratch_rows), int(mem_budget_bytes))
         h = ctypes.c_void_p()
         check(lib.ts_server_create(index.handle, ctypes.byref(p), ctypes.byref(h)))
         self._h = h
@@ -520,7 +535,16 @@ class Server:
         check(lib.ts_server_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(out),
                                  ctypes.byref(tm)))
         return Result(out, 0), {"submit_us": tm.submit_us, "start_us": tm.start_us,
-                                "done_us": tm.done_us, "batch_requests": int(tm.batch_requests)}
+                                "done_us": tm.done_us, "batch_requests": int(tm.batch_requests),
+                                "requeued": int(tm.requeued)}
+
+    def info(self) -> dict:
+        """Device-memory accounting: budget, bytes held by the plans, bytes of live result rows."""
+        lib = _lib.load()
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib.ts_server_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"budget_bytes": int(a.value), "plan_bytes": int(b.value),
+                "held_bytes": int(c.value)}
 
     def cancel(self, ticket):
         check(_lib.load().ts_server_cancel(self._h, int(ticket)))

@@ -84,6 +84,29 @@ ts_status ts_measure_alu_peaks(double *fp32_tflops, double *fp64_tflops)
     });
 }
 
+ts_status ts_eval_refined_estimates(const double *x, uint64_t n, double *rcp_est,
+                                     double *sqrt_est, double *rcp_ref, double *sqrt_ref)
+{
+    if (n && (!x || !rcp_est || !sqrt_est || !rcp_ref || !sqrt_ref)) {
+        set_error("ts_eval_refined_estimates: NULL argument");
+        return TS_ERR_INVALID_ARG;
+    }
+    return guarded([&]() -> ts_status {
+        ts_status st = eval_estimates(x, n, rcp_est, sqrt_est, rcp_ref, sqrt_ref);
+        return st == TS_OK ? clear_error(st) : st;
+    });
+}
+
+ts_status ts_debug_inject_stall(uint64_t limit_ns)
+{
+    if (limit_ns == 0 || limit_ns > 1000000000ull) {
+        set_error("ts_debug_inject_stall: limit must be in (0, 1e9] ns");
+        return TS_ERR_INVALID_ARG;
+    }
+    inject_stall(limit_ns);
+    return clear_error(TS_OK);
+}
+
 uint64_t ts_kernel_launches(void) { return (uint64_t)ts::launch_count(); }
 
 ts_status ts_search_brute_noalloc(const ts_segments *db, const ts_segments *q,
@@ -431,6 +454,18 @@ ts_status ts_server_wait(ts_server *h, uint64_t ticket, uint32_t timeout_ms, ts_
         *out = r;
         return clear_error(TS_OK);
     });
+}
+
+ts_status ts_server_info(ts_server *srv, uint64_t *budget_bytes, uint64_t *plan_bytes,
+                         uint64_t *held_bytes)
+{
+    Server *s = as_server(srv);
+    if (!s) {
+        set_error("ts_server_info: invalid server handle");
+        return TS_ERR_INVALID_ARG;
+    }
+    server_info(s, budget_bytes, plan_bytes, held_bytes);
+    return clear_error(TS_OK);
 }
 
 ts_status ts_server_cancel(ts_server *h, uint64_t ticket)

@@ -527,6 +527,8 @@ ts_status RowBlock::alloc(uint64_t n, cudaStream_t s)
     TS_CUDA(pool_malloc((void **)&e, sizeof(uint32_t) * n, s));
     TS_CUDA(pool_malloc((void **)&tin, sizeof(double) * n, s));
     TS_CUDA(pool_malloc((void **)&tout, sizeof(double) * n, s));
+    bytes = ROW_BYTES * n;
+    if (held) held->fetch_add((int64_t)bytes);
     return TS_OK;
 }
 
@@ -538,6 +540,7 @@ RowBlock::~RowBlock()
     if (e) cudaFreeAsync(e, 0);
     if (tin) cudaFreeAsync(tin, 0);
     if (tout) cudaFreeAsync(tout, 0);
+    if (held && bytes) held->fetch_sub((int64_t)bytes);
 }
 
 }  // namespace ts

@@ -1,6 +1,7 @@
 // ts_batch.cuh -- batch plans (reusable pipelines with fixed capacities) and shared row blocks.
 #pragma once
 
+#include <atomic>
 #include <memory>
 #include <vector>
 
@@ -56,13 +57,18 @@ struct BatchPlan {
     uint32_t last_nreq = 0;
 };
 
-// Device rows shared by the results of a one-shot batch.
+// Device rows shared by the results of a one-shot batch or a served batch. `held`, when set,
+// counts the bytes of live row blocks (the served loop's admission): alloc adds the block's
+// bytes, the destructor (when the last result using the rows is released) subtracts them.
 struct RowBlock {
     uint32_t *q = nullptr, *e = nullptr;
     double *tin = nullptr, *tout = nullptr;
+    std::shared_ptr<std::atomic<int64_t>> held;
+    uint64_t bytes = 0;
     ts_status alloc(uint64_t n, cudaStream_t s);
     ~RowBlock();
 };
+constexpr uint64_t ROW_BYTES = 2 * sizeof(uint32_t) + 2 * sizeof(double);
 
 void note_launches(unsigned long long n);
 

@@ -62,20 +62,28 @@ static __device__ __forceinline__ uint64_t globaltimer_ns()
     return t;
 }
 
-// Bounded wait on an mbarrier phase: gives up after ~2 s of wall time.
-static __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity)
+// Limit of every bounded wait on a copy: 2 s of wall time.
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+
+// Bounded wait on an mbarrier phase: gives up (false) after limit_ns of wall time.
+static __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity,
+                                                         uint64_t limit_ns = WAIT_LIMIT_NS)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0 && globaltimer_ns() - t0 > 2000000000ull) return false;
+        if ((it & 255u) == 0 && globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 
 // ---------------------------------------------------------------------------------------------
-// exact FP64 interaction test (same operation order as the plain definition; no contraction)
+// exact FP64 interaction test
 // ---------------------------------------------------------------------------------------------
+// Every multiply-add of the test is an explicit fma() (one FP64 instruction and one rounding; the
+// rest of the library is compiled without contraction, so the rounding of each step is exactly
+// the one written here). The test differs from the plain definition's evaluation by a few
+// rounding errors, which only matters for pairs whose minimum separation is within rounding of d.
 static __device__ __forceinline__ double dmx(double a, double b) { return a > b ? a : b; }
 static __device__ __forceinline__ double dmn(double a, double b) { return a < b ? a : b; }
 
@@ -84,34 +92,71 @@ struct Quad {
 };
 
 // Window and quadratic coefficients; false when the common window has no positive length.
+// r0 = p_q(t_lo) - p_l(t_lo), dv = v_q - v_l, a = dv.dv, b = r0.dv, c = r0.r0 - d^2.
 static __device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e, double dd, Quad &o)
 {
-    double t_lo = dmx(q.w0, e.t0);
-    double t_hi = dmn(q.w1, e.t1);
+    const double t_lo = dmx(q.w0, e.t0);
+    const double t_hi = dmn(q.w1, e.t1);
     if (!(t_lo < t_hi)) return false;
-    double dq = t_lo - q.t0, de = t_lo - e.t0;
-    double rx = (q.x0 + q.vx * dq) - (e.x0 + e.vx * de);
-    double ry = (q.y0 + q.vy * dq) - (e.y0 + e.vy * de);
-    double rz = (q.z0 + q.vz * dq) - (e.z0 + e.vz * de);
-    double dvx = q.vx - e.vx, dvy = q.vy - e.vy, dvz = q.vz - e.vz;
+    const double dq = t_lo - q.t0, de = t_lo - e.t0;
+    const double rx = fma(q.vx, dq, q.x0) - fma(e.vx, de, e.x0);
+    const double ry = fma(q.vy, dq, q.y0) - fma(e.vy, de, e.y0);
+    const double rz = fma(q.vz, dq, q.z0) - fma(e.vz, de, e.z0);
+    const double dvx = q.vx - e.vx, dvy = q.vy - e.vy, dvz = q.vz - e.vz;
     o.t_lo = t_lo;
     o.T = t_hi - t_lo;
-    o.a = (dvx * dvx + dvy * dvy) + dvz * dvz;
-    o.b = (rx * dvx + ry * dvy) + rz * dvz;
-    o.c = ((rx * rx + ry * ry) + rz * rz) - dd;
+    o.a = fma(dvz, dvz, fma(dvy, dvy, dvx * dvx));
+    o.b = fma(rz, dvz, fma(ry, dvy, rx * dvx));
+    o.c = fma(rz, rz, fma(ry, ry, fma(rx, rx, -dd)));
     return true;
 }
 
 // Division-free hit decision: the minimum of a tau^2 + 2 b tau + c over [0, T] is <= 0.
 static __device__ __forceinline__ bool quad_hit(const Quad &k)
 {
-    if (k.a == 0.0) return k.c <= 0.0;
-    if (k.b >= 0.0) return k.c <= 0.0;                       // minimum at tau = 0
-    if (-k.b >= k.a * k.T) return (k.a * k.T + 2.0 * k.b) * k.T + k.c <= 0.0;  // at tau = T
-    return k.b * k.b - k.a * k.c >= 0.0;                     // interior minimum
+    if (k.a == 0.0 || k.b >= 0.0) return k.c <= 0.0;        // minimum at tau = 0
+    const double aT = k.a * k.T;
+    if (-k.b >= aT) return fma(aT + 2.0 * k.b, k.T, k.c) <= 0.0;  // at tau = T
+    return fma(k.b, k.b, -(k.a * k.c)) >= 0.0;               // interior minimum
 }
 
-// Interval of a hit from the numerically stable root pair s/a, c/s.
+// |x| within [2^-1000, 2^1000) (its biased exponent, sign ignored): the range where the refined
+// estimates below are accurate (no subnormal estimate, no overflow of x * y).
+static __device__ __forceinline__ bool nr_range(double x)
+{
+    const uint32_t ex = ((uint32_t)__double2hiint(x) >> 20) & 0x7ffu;
+    return ex - 23u < 2000u;
+}
+
+// 1/x by Newton-Raphson from the hardware estimate (rcp.approx.ftz.f64, about 20 good bits): one
+// third-order step y + y e + y e^2 with e = 1 - x y cubes the estimate's relative error, leaving
+// only the rounding of the last steps (a few ulps). For x in the nr_range.
+static __device__ __forceinline__ double rcp_nr(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
+}
+
+// sqrt(x) by Newton-Raphson from the hardware estimate of 1/sqrt(x) (rsqrt.approx.ftz.f64): the
+// coupled iteration on g ~ sqrt(x), h ~ 1/(2 sqrt(x)) (r = 1/2 - g h; g += g r; h += h r), then
+// one Newton correction of g with the residual x - g^2. For x in the nr_range.
+static __device__ __forceinline__ double sqrt_nr(double x)
+{
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double g = x * y, h = 0.5 * y;
+    const double r = fma(-g, h, 0.5);
+    g = fma(g, r, g);
+    h = fma(h, r, h);
+    return fma(fma(-g, g, x), h, g);
+}
+
+// Interval of a hit from the numerically stable root pair s/a, c/s (s = -(b + sign(b) sqrt(disc)),
+// disc = b^2 - a c). The square root and the two quotients come from the refined estimates
+// above (relative error of a few ulps, far inside the 1e-9 interval tolerance); values outside
+// their range take the library's sqrt and division.
 static __device__ __forceinline__ void quad_interval(const Quad &k, double *tin, double *tout)
 {
     double lower, upper;
@@ -119,17 +164,17 @@ static __device__ __forceinline__ void quad_interval(const Quad &k, double *tin,
         lower = 0.0;
         upper = k.T;
     } else {
-        double disc = k.b * k.b - k.a * k.c;
+        double disc = fma(k.b, k.b, -(k.a * k.c));
         if (disc < 0.0) disc = 0.0;  // only reachable within rounding of a tangency
-        double sq = sqrt(disc);
-        double s = -(k.b + copysign(sq, k.b));
+        const double sq = nr_range(disc) ? sqrt_nr(disc) : sqrt(disc);
+        const double s = -(k.b + copysign(sq, k.b));
         double r1, r2;
         if (s == 0.0) {
             r1 = 0.0;
             r2 = 0.0;
         } else {
-            r1 = s / k.a;
-            r2 = k.c / s;
+            r1 = nr_range(k.a) ? s * rcp_nr(k.a) : s / k.a;
+            r2 = nr_range(s) ? k.c * rcp_nr(s) : k.c / s;
         }
         lower = dmx(0.0, dmn(r1, r2));
         upper = dmn(k.T, dmx(r1, r2));

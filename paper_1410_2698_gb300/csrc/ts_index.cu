@@ -436,6 +436,13 @@ ts_status build_grid(Ctx &c, Index *ix, const double *lo3, const double *hi3)
     TS_CHECK(ix->alloc(&ix->ga_rec, n));
     k_gather_rec<<<nblocks(n), TPB, 0, c.s>>>(ix->ga, n, ix->rec, ix->ga_rec);
     TS_LAUNCHED();
+    // chunk bounding records: the cell sort is stable over the start-time order, so a chunk of
+    // a cell spans a short stretch of time and a query's window skips most of a cell's chunks
+    const uint64_t nchunks = (n + 63) / 64;
+    TS_CHECK(ix->alloc(&ix->gbox, nchunks));
+    const unsigned cb = (unsigned)std::min<uint64_t>((nchunks * 32 + TPB - 1) / TPB, 152 * 32);
+    k_chunk_box<<<cb, TPB, 0, c.s>>>(ix->ga_rec, n, nchunks, ix->gbox);
+    TS_LAUNCHED();
     ix->g_len = n;
     return c.read_status();
 }

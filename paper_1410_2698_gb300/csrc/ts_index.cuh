@@ -50,11 +50,13 @@ struct Index {
 
     // flatly structured grid (Sec. 4.1), one cell per entry (the cell of its MBB's minimum
     // corner): dense cell offsets over g^3 cells and the lookup array A with a copy of each
-    // entry's prefilter record
+    // entry's prefilter record; inside a cell the entries keep their start-time order, so the
+    // bounding records of its chunks are narrow in time
     uint32_t g = 0;
     double g_lo[3] = {0, 0, 0}, g_w[3] = {0, 0, 0};
     uint32_t *ga = nullptr;
     RecF *ga_rec = nullptr;
+    RecF *gbox = nullptr;  // bounding record of every aligned chunk of 64 of ga_rec
     uint32_t *g_off = nullptr;  // g^3 + 1
     double *g_bound[3] = {nullptr, nullptr, nullptr};  // lo + j*w for j = 0..g
     uint64_t g_len = 0;

@@ -192,6 +192,8 @@ inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t
 // Stream-ordered allocation from the library's pool (freed blocks stay pooled); inside a stream
 // capture a graph memory node. Release with cudaFreeAsync.
 cudaError_t pool_malloc(void **p, size_t nbytes, cudaStream_t stream);
+// Return the pool's unused memory of the current device to the device (synchronises it).
+void pool_trim();
 
 struct DevBuf {
     void *p = nullptr;

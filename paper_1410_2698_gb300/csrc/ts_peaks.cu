@@ -1,8 +1,11 @@
-// ts_peaks.cu -- measured arithmetic peaks of this GPU (FP32 and FP64 fused multiply-add
-// throughput), the denominators of the pair kernel's roofline. Every thread runs independent
-// chains of FMA (explicit fmaf / fma, so the count is exact whatever the contraction flags) over
-// a grid that fills every SM; the time comes from CUDA events around the launch.
-#include "ts_internal.cuh"
+// ts_peaks.cu -- diagnostics: measured arithmetic peaks of this GPU (FP32 and FP64 fused
+// multiply-add throughput), the denominators of the pair kernel's roofline, and an evaluation of
+// the exact test's refined reciprocal and square root beside the CUDA runtime's.
+//
+// Peaks: every thread runs independent chains of FMA (explicit fmaf / fma, so the count is exact
+// whatever the contraction flags) over a grid that fills every SM; the time comes from CUDA
+// events around the launch.
+#include "ts_device.cuh"
 
 namespace ts {
 
@@ -60,7 +63,42 @@ ts_status time_fma(int blocks, int iters, double *tflops)
     return TS_OK;
 }
 
+// The exact test's refined estimates (rcp_nr, sqrt_nr) and the CUDA runtime's correctly rounded
+// 1/x and sqrt(x) of the same inputs; NaN where x is outside the estimates' range.
+__global__ void k_eval_estimates(const double *x, uint64_t n, double *out)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    const bool in = nr_range(v);
+    out[i] = in ? rcp_nr(v) : NAN;
+    out[n + i] = in && v > 0.0 ? sqrt_nr(v) : NAN;
+    out[2 * n + i] = 1.0 / v;
+    out[3 * n + i] = sqrt(v);
+}
+
 }  // namespace
+
+ts_status eval_estimates(const double *x, uint64_t n, double *rcp_est, double *sqrt_est,
+                         double *rcp_ref, double *sqrt_ref)
+{
+    if (n == 0) return TS_OK;
+    double *d = nullptr;
+    TS_CUDA(cudaMalloc((void **)&d, sizeof(double) * 5 * n));
+    cudaError_t e = cudaMemcpy(d, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_eval_estimates<<<(unsigned)((n + 255) / 256), 256>>>(d, n, d + n);
+        note_launches(1);
+        e = cudaGetLastError();
+    }
+    double *outs[4] = {rcp_est, sqrt_est, rcp_ref, sqrt_ref};
+    for (int k = 0; k < 4 && e == cudaSuccess; k++)
+        e = cudaMemcpy(outs[k], d + (uint64_t)(k + 1) * n, sizeof(double) * n,
+                       cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_status(e, "eval_estimates");
+    return TS_OK;
+}
 
 ts_status measure_alu_peaks(double *fp32_tflops, double *fp64_tflops)
 {

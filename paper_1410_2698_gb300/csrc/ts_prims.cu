@@ -80,6 +80,13 @@ static cudaMemPool_t work_pool()
     return pools[dev];
 }
 
+void pool_trim()
+{
+    cudaMemPool_t pool = work_pool();
+    if (pool && cudaDeviceSynchronize() == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    cudaGetLastError();
+}
+
 cudaError_t pool_malloc(void **p, size_t nbytes, cudaStream_t stream)
 {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -21,12 +21,13 @@
 //   2. FP32 gap test: squared MBB distance accumulated rounding down against an upper bound of
 //      d^2 (run only when some lane passed stage 1); a pair is dropped only when a lower bound
 //      of its separation exceeds d, so no pair the FP64 test could accept is ever dropped;
-//   3. the exact FP64 test on the survivors (the closed form of the interaction, evaluated
-//      without FMA contraction so it reproduces the plain definition's rounding), run 32 at a
-//      time on survivors compacted with ballot/popc so the FP64 pipe runs full warps.
+//   3. the exact FP64 test on the survivors (the closed form of the interaction with explicit
+//      fused multiply-adds; a hit's square root and quotients from refined hardware estimates),
+//      run 32 at a time on survivors compacted with ballot/popc so the FP64 pipe runs full warps.
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "ts_device.cuh"
@@ -646,12 +647,18 @@ struct __align__(16) WarpSmem {
     uint32_t plist[PK_PLIST];  // (member << 8 | slot) pairs of a chunk that passed the box test
     unsigned long long bar[PK_STAGES];
     unsigned long long mbar;  // members + chunk boxes
+    unsigned long long xbar;  // injected stall (tests): a barrier nothing ever arrives on
     // counts of the count pass: chunks, bitmask chunks, sparse member visits, survivors (then,
     // at the end, the warp's tests, FP64 tests and hits; the last slot pads to 64 bytes)
     unsigned long long sweep[8];
 };
 
 enum { PASS_COUNT = 0, PASS_WRITE = 1 };
+
+// Flag in a tile descriptor's group word, set by the count pass on a tile with a hit that the
+// scratch did not keep: the write pass sweeps exactly the flagged tiles (k_place writes the rows
+// of the kept hits, the same rows the sweep gives them).
+constexpr uint32_t TILE_REDO = 0x80000000u;
 
 struct PairParams {
     PipeBufs b;
@@ -665,6 +672,9 @@ struct PairParams {
     uint64_t rows_cap;  // write pass: rows beyond this capacity are not written (flagged)
     uint64_t scap;      // hits the count pass keeps for placement (0: none)
     uint32_t tile;      // records per tile
+    // > 0 (tests only): the first warp of block 0 waits this long on a barrier phase that never
+    // completes before taking any tile, so the kernel's timeout path runs (status, return)
+    uint64_t stall_ns;
 };
 
 // Exact FP64 test of one (query, entry) pair and, when `interval`, its hit interval. Not inlined:
@@ -705,6 +715,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         for (int k = 0; k < 4; k++) W.sweep[k] = 0;
         for (int k = 0; k < PK_STAGES; k++) mbar_init(&W.bar[k], 1);
         mbar_init(&W.mbar, 1);
+        mbar_init(&W.xbar, 1);
         fence_mbar_init();
     }
     __syncwarp();
@@ -716,11 +727,14 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         pending[k] = false;
     }
     bool abort = false;
+    if (P.stall_ns && blockIdx.x == 0 && wid == 0)
+        abort = !mbar_wait_bounded(&W.xbar, 0u, P.stall_ns);  // (never arrived on: times out)
 
     uint64_t ntiles = (uint64_t)B.hdr[HDR_T_LO] | ((uint64_t)B.hdr[HDR_T_HI] << 32);
     if (ntiles > P.tcap || ntiles > PK_MAX_TILES) ntiles = 0;  // overflow already flagged
     if (PASS == PASS_WRITE && P.scap && B.stats[ST_SCRATCH] <= P.scap)
         ntiles = 0;  // the count pass kept every hit: k_place writes the rows
+    // (otherwise the write pass sweeps only the tiles whose hits were not all kept)
     if (PASS == PASS_WRITE && ntiles && B.tile_off[ntiles] > P.rows_cap) {
         // more rows than the output holds: write none (the caller sees the exact count)
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(B.status, DEV_ERR_OVERFLOW);
@@ -778,7 +792,8 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 if (lane == 0) base = atomicAdd(&B.stats[ST_SCRATCH], (unsigned long long)__popc(hm));
                 base = __shfl_sync(FULL, base, 0);
                 const unsigned long long slot = base + __popc(hm & lt_mask);
-                if (h && slot < P.scap && interval) {
+                const bool kept = h && slot < P.scap && interval;
+                if (kept) {
                     B.s_tile[slot] = tile;
                     B.s_rank[slot] = rank;
                     B.s_q[slot] = ql;
@@ -786,6 +801,10 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                     B.s_tin[slot] = tin;
                     B.s_tout[slot] = tout;
                 }
+                // a tile with a hit the scratch could not keep is swept again by the write pass
+                const unsigned lost = __ballot_sync(FULL, h && !kept);
+                if (h && !kept && (mine & lost & lt_mask) == 0)
+                    atomicOr(&B.tdesc[tile].x, TILE_REDO);
             }
         } else if (h) {
             const uint64_t o = B.tile_off[tile] + rank;
@@ -815,12 +834,14 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
     while (!abort && t < ntiles) {
         uint64_t t_next = 0;
         if (lane == 0) t_next = nwarps + (uint64_t)atomicAdd(&B.counters[PASS], 1u);
-        if (PASS == PASS_WRITE && B.tile_hits[t] == 0) {  // no rows in this tile
+        if (PASS == PASS_WRITE &&
+            (B.tile_hits[t] == 0 || (P.scap && !(D.x & TILE_REDO)))) {
+            // no rows in this tile, or every one of them was kept by the count pass
             t = __shfl_sync(FULL, t_next, 0);
             D = t < ntiles ? B.tdesc[t] : make_uint4(0u, 0u, 0u, 0u);
             continue;
         }
-        const uint32_t g = D.x, s0 = D.y, s1 = D.z;
+        const uint32_t g = D.x & ~TILE_REDO, s0 = D.y, s1 = D.z;
         const uint32_t sel = D.w & 7u, count = ((D.w >> 3) & 31u) + 1u;
         const uint32_t tw = (uint32_t)t | (sel << 29);
         const RecF *recs = P.rec[sel];
@@ -1095,13 +1116,13 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
 }
 
 // Rows of the hits the count pass kept: row = the tile's scanned offset + the hit's rank in the
-// tile, the same row the write pass's sweep would give it. Does nothing when the scratch
-// overflowed (the write pass sweeps instead) or the rows exceed the output capacity.
+// tile, the same row the write pass's sweep would give it. When the scratch overflowed, the
+// tiles it could not hold are swept again by the write pass (which writes the same values to the
+// rows placed here). Does nothing when the rows exceed the output capacity.
 __global__ void k_place(PipeBufs b, uint64_t scap, uint64_t tcap, uint64_t rows_cap)
 {
     pdl_enter();
-    const unsigned long long n = b.stats[ST_SCRATCH];
-    if (n > scap) return;
+    const unsigned long long n = min((unsigned long long)scap, b.stats[ST_SCRATCH]);
     const uint64_t T = (uint64_t)b.hdr[HDR_T_LO] | ((uint64_t)b.hdr[HDR_T_HI] << 32);
     if (T > tcap || T > PK_MAX_TILES) return;  // overflow already flagged
     if (b.tile_off[T] > rows_cap) {
@@ -1161,13 +1182,18 @@ void fill_pair_params(PairParams &P, const Index *ix, const ReqDesc *reqs, const
     P.box[SEL_T] = ix->tbox;
     P.rec[SEL_GRID] = ix->ga_rec;
     P.ids[SEL_GRID] = ix->ga;
+    P.box[SEL_GRID] = ix->gbox;
     P.seg = ix->seg;
     P.orig = ix->orig;
     P.tcap = c.tiles;
     P.rows_cap = c.rows;
     P.scap = c.scratch;
     P.tile = c.tile;
+    P.stall_ns = 0;
 }
+
+// A stall requested for the next count pass (tests of the timeout path), taken by that launch.
+std::atomic<uint64_t> g_stall_ns{0};
 
 // Two CUDA events bracketing one kernel launch on its stream.
 struct EventPair {
@@ -1333,7 +1359,8 @@ ts_status pipe_group(const Index *ix, const ReqDesc *reqs, uint32_t nreq, const 
                   nreq, b);
     const unsigned gblk = (unsigned)std::min<uint64_t>((c.groups * 32 + TPB - 1) / TPB, 152 * 16);
     TS_LAUNCH_PDL(k_groups, dim3(gblk), dim3(TPB), 0, s,
-                  nreq, c.groups, c.tile, ix->tbox ? (1u << SEL_T) : 0u, reqs, b);
+                  nreq, c.groups, c.tile,
+                  (ix->tbox ? (1u << SEL_T) : 0u) | (ix->gbox ? (1u << SEL_GRID) : 0u), reqs, b);
     TS_CHECK(scan_u32_to_u64(b.ntiles, b.tile_base, c.groups, s, b.hdr + HDR_G));
     if (host_tiles) {  // the caller reads the tile count before the count pass
         TS_LAUNCH_PDL(k_hdr, dim3(1), dim3(1), 0, s,
@@ -1350,6 +1377,7 @@ ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
     if (c.pair_blocks > 0 && c.pair_blocks < blocks) blocks = c.pair_blocks;
     PairParams P;
     fill_pair_params(P, ix, reqs, b, c);
+    P.stall_ns = c.stall_ns;
     if (c.tiles) {
         const unsigned dblk = (unsigned)std::min<uint64_t>((c.groups * 32 + TPB - 1) / TPB, 152 * 16);
         TS_LAUNCH_PDL(k_tile_desc, dim3(dblk), dim3(TPB), 0, s,
@@ -1359,6 +1387,8 @@ ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, co
     }
     return TS_OK;
 }
+
+void inject_stall(uint64_t ns) { g_stall_ns.store(ns); }
 
 ts_status pipe_scan_rows(const PipeBufs &b, const PipeCaps &c, cudaStream_t s)
 {
@@ -1618,6 +1648,7 @@ ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_par
     EventPair ev_count, ev_write;
     TS_CHECK(ev_count.create());
     TS_CHECK(ev_write.create());
+    c.stall_ns = g_stall_ns.exchange(0);  // (a stall requested by a test of the timeout path)
     TS_CUDA(cudaEventRecord(ev_count.a, s));
     TS_CHECK(pipe_count(ix, w.reqdesc.as<ReqDesc>(), b, c, s));
     TS_CUDA(cudaEventRecord(ev_count.b, s));

@@ -94,6 +94,7 @@ struct PipeCaps {
     uint32_t tile = PK_TILE;  // records per tile (multiple of PK_CH)
     int pair_blocks = 0;      // pair kernel grid (0 = all resident blocks)
     uint64_t scratch = 0;     // hits the count pass keeps for placement (0: the write pass sweeps)
+    uint64_t stall_ns = 0;    // plain searches only, tests of the timeout path (inject_stall)
 };
 constexpr uint64_t SCRATCH_MAX = 1ull << 24;  // rows (32 B each)
 
@@ -112,6 +113,8 @@ unsigned long long launch_count();
 ts_status search_plain(const Index *ix, const ts_segments *q, const ts_query_params *qp,
                        cudaStream_t s, SearchOut *out);
 ts_status measure_alu_peaks(double *fp32_tflops, double *fp64_tflops);
+ts_status eval_estimates(const double *x, uint64_t n, double *rcp_est, double *sqrt_est,
+                         double *rcp_ref, double *sqrt_ref);
 ts_status search_points(const Index *ix, const double *x, const double *y, const double *z,
                         uint64_t n, bool on_host, const ts_query_params *qp, cudaStream_t s,
                         SearchOut *out);
@@ -130,6 +133,9 @@ ts_status pipe_group(const Index *ix, const ReqDesc *reqs, uint32_t nreq, const 
 ts_status pipe_count(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,
                      cudaStream_t s);
 ts_status pipe_scan_rows(const PipeBufs &b, const PipeCaps &c, cudaStream_t s);
+// Tests of the timeout path: the count pass of the next plain search stalls one warp for ns
+// nanoseconds on a barrier phase that never completes, then takes the timeout path.
+void inject_stall(uint64_t ns);
 ts_status pipe_write(const Index *ix, const ReqDesc *reqs, const PipeBufs &b, const PipeCaps &c,
                      cudaStream_t s);
 // Layout of a unit's sort key: request | array (sel_bits) | top lo_bits bits of the range start.

@@ -5,15 +5,18 @@
 // capacities allow, and runs them on up to max_inflight batch plans, each with its own stream:
 // requests that arrive while a batch is on the device go into the next free plan, so batches
 // overlap on the device. A batch runs in two phases: its plan (a CUDA graph) runs up to the count
-// pass and the row scan; the loop then allocates exactly the batch's rows from the library's
-// pool (admission by the memory the result needs) and launches the write phase into them. A
-// batch with more rows than max_batch_rows, or that outgrew a work capacity, is split and re-run;
-// a lone request that cannot fit ends with TS_ERR_CAPACITY. Completed requests share the batch's
-// row block (each result is a view of its rows) and carry host timestamps. Every wait -- client
-// waits and the loop's idle waits -- is bounded.
+// pass and the row scan; the loop then admits the batch's exact rows against the server's
+// device-memory budget (its plans plus the rows of results not yet released) -- a batch whose
+// rows do not fit beside the rows still held waits, its plan idle, until results are released --
+// allocates them from the library's pool and launches the write phase into them. A batch with
+// more rows than max_batch_rows or than the budget holds, or that outgrew a work capacity, is
+// split or its plan grown, and re-run; a lone request that cannot fit ends with TS_ERR_CAPACITY.
+// Completed requests share the batch's row block (each result is a view of its rows) and carry
+// host timestamps. Every wait -- client waits and the loop's idle waits -- is bounded.
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -38,6 +41,7 @@ struct SrvReq {
     ts_query_params qp{};
     double submit_us = 0, start_us = 0, done_us = 0;
     uint32_t batch_requests = 0;
+    uint32_t requeued = 0;  // times its batch went back to the queue
     int state = RQ_QUEUED;
     ts_status status = TS_OK;
     std::string error;
@@ -45,7 +49,9 @@ struct SrvReq {
     std::shared_ptr<RowBlock> block;  // the batch's rows (out points into them)
 };
 
-enum { SLOT_IDLE = 0, SLOT_COUNT = 1, SLOT_WRITE = 2 };
+// A slot's phases: its batch's count phase on the device, waiting for room in the memory
+// budget for its rows (the plan idle, holding the count phase's offsets), the write phase.
+enum { SLOT_IDLE = 0, SLOT_COUNT = 1, SLOT_ADMIT = 2, SLOT_WRITE = 3 };
 
 struct Slot {
     BatchPlan *plan = nullptr;
@@ -53,6 +59,7 @@ struct Slot {
     std::vector<SrvReq *> batch;
     bool busy = false;
     int phase = SLOT_IDLE;
+    uint64_t rows = 0;  // the batch's rows (count phase done)
     std::shared_ptr<RowBlock> block;
 };
 
@@ -72,7 +79,13 @@ struct Server {
     bool stop = false;
     uint64_t next_ticket = 1;
     size_t split_limit = 0;  // after an overflow: at most this many requests in the next batch
+    // device-memory budget: the plans' own bytes, and the bytes of live row blocks (updated by
+    // the blocks themselves, also after the server is gone)
+    uint64_t budget = 0, plan_bytes = 0;
+    std::shared_ptr<std::atomic<int64_t>> held = std::make_shared<std::atomic<int64_t>>(0);
     std::chrono::steady_clock::time_point t0;
+
+    uint64_t row_budget() const { return budget > plan_bytes ? budget - plan_bytes : 0; }
 
     double now_us() const
     {
@@ -100,6 +113,7 @@ void split_batch(Server *s, std::vector<SrvReq *> &batch, const char *why)
     } else {
         for (size_t i = batch.size(); i-- > 0;) {
             batch[i]->state = RQ_QUEUED;
+            batch[i]->requeued++;
             s->queue.push_front(batch[i]);
         }
         s->split_limit = std::max<size_t>(1, batch.size() / 2);
@@ -108,8 +122,11 @@ void split_batch(Server *s, std::vector<SrvReq *> &batch, const char *why)
     s->cv_done.notify_all();
 }
 
-// The count phase of a slot's batch completed: allocate its rows and launch the write phase, or
-// end the batch (no rows, an error, or a split).
+void end_batch(Server *s, Slot &sl, ts_status st);
+void try_admit(Server *s, Slot &sl);
+
+// The count phase of a slot's batch completed: admit its rows (try_admit), or end the batch (no
+// rows, an error), split it or grow its plan.
 void count_done(Server *s, Slot &sl)
 {
     ts_batch_status bs;
@@ -140,11 +157,14 @@ void count_done(Server *s, Slot &sl)
         }
         BatchPlan *np = nullptr;
         if (grow && create_plan(p->ix, &bp, nullptr, false, &np) == TS_OK) {
+            s->plan_bytes += np->dbytes;
+            s->plan_bytes -= std::min(s->plan_bytes, (uint64_t)p->dbytes);
             destroy_plan(p);
             sl.plan = np;
             std::lock_guard<std::mutex> lk(s->mu);
             for (size_t i = sl.batch.size(); i-- > 0;) {
                 sl.batch[i]->state = RQ_QUEUED;
+                sl.batch[i]->requeued++;
                 s->queue.push_front(sl.batch[i]);
             }
             sl.batch.clear();
@@ -153,38 +173,27 @@ void count_done(Server *s, Slot &sl)
             return;
         }
     }
-    if (st == TS_OK && (bs.overflow || bs.rows > s->prm.max_batch_rows)) {
+    if (st == TS_OK && (bs.overflow || bs.rows > s->prm.max_batch_rows ||
+                        ROW_BYTES * bs.rows > s->row_budget())) {
         std::lock_guard<std::mutex> lk(s->mu);
-        split_batch(s, sl.batch, "request exceeds the server's per-batch row or work capacity");
+        split_batch(s, sl.batch, "request exceeds the server's per-batch row, memory or work "
+                                 "capacity");
         sl.busy = false;
         sl.phase = SLOT_IDLE;
         return;
     }
     if (st == TS_OK && bs.rows > 0) {
-        BatchPlan *p = sl.plan;
-        auto block = std::make_shared<RowBlock>();
-        st = block->alloc(bs.rows, p->stream);
-        if (st == TS_OK) {
-            p->b.out_q = block->q;
-            p->b.out_e = block->e;
-            p->b.out_tin = block->tin;
-            p->b.out_tout = block->tout;
-            p->caps.rows = bs.rows;
-            st = pipe_write(p->ix, p->d_reqs, p->b, p->caps, p->stream);
-        }
-        if (st == TS_OK) {
-            cudaError_t e = cudaMemcpyAsync(&p->h_out->status, p->b.status, 4,
-                                            cudaMemcpyDeviceToHost, p->stream);
-            if (e == cudaSuccess) e = cudaEventRecord(sl.done, p->stream);
-            if (e != cudaSuccess) st = cuda_status(e, "server write phase");
-        }
-        if (st == TS_OK) {
-            sl.block = block;
-            sl.phase = SLOT_WRITE;
-            return;
-        }
+        sl.rows = bs.rows;
+        sl.phase = SLOT_ADMIT;
+        try_admit(s, sl);
+        return;
     }
-    // no rows, or a failure: the batch ends here
+    end_batch(s, sl, st);
+}
+
+// End a slot's batch without rows (none found, or a failure).
+void end_batch(Server *s, Slot &sl, ts_status st)
+{
     std::lock_guard<std::mutex> lk(s->mu);
     const char *msg = st == TS_OK ? nullptr : last_error();
     for (SrvReq *q : sl.batch) {
@@ -197,6 +206,45 @@ void count_done(Server *s, Slot &sl)
     sl.phase = SLOT_IDLE;
     if (st == TS_OK) s->split_limit = 0;
     s->cv_done.notify_all();
+}
+
+// Admission of a counted batch's rows: when they fit in the budget beside the rows still held
+// (or nothing else is held), allocate them and launch the write phase; otherwise the slot stays
+// in SLOT_ADMIT and the loop tries again. An allocation that fails while other rows are held is
+// retried the same way.
+void try_admit(Server *s, Slot &sl)
+{
+    const uint64_t need = ROW_BYTES * sl.rows;
+    const int64_t held = s->held->load();
+    if (held > 0 && (uint64_t)held + need > s->row_budget()) return;  // wait for releases
+    BatchPlan *p = sl.plan;
+    auto block = std::make_shared<RowBlock>();
+    block->held = s->held;
+    ts_status st = block->alloc(sl.rows, p->stream);
+    if (st == TS_ERR_OOM && held > 0) {
+        cudaGetLastError();
+        return;  // retry after results are released
+    }
+    if (st == TS_OK) {
+        p->b.out_q = block->q;
+        p->b.out_e = block->e;
+        p->b.out_tin = block->tin;
+        p->b.out_tout = block->tout;
+        p->caps.rows = sl.rows;
+        st = pipe_write(p->ix, p->d_reqs, p->b, p->caps, p->stream);
+    }
+    if (st == TS_OK) {
+        cudaError_t e = cudaMemcpyAsync(&p->h_out->status, p->b.status, 4,
+                                        cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(sl.done, p->stream);
+        if (e != cudaSuccess) st = cuda_status(e, "server write phase");
+    }
+    if (st == TS_OK) {
+        sl.block = block;
+        sl.phase = SLOT_WRITE;
+        return;
+    }
+    end_batch(s, sl, st);
 }
 
 // The write phase of a slot's batch completed: every request gets a view of its rows.
@@ -292,6 +340,13 @@ void loop(Server *s)
         bool progressed = false;
         for (Slot &sl : s->slots) {
             if (!sl.busy) continue;
+            if (sl.phase == SLOT_ADMIT) {  // waiting for room for its rows
+                lk.unlock();
+                try_admit(s, sl);
+                lk.lock();
+                progressed = progressed || sl.phase != SLOT_ADMIT;
+                continue;
+            }
             cudaError_t q = cudaEventQuery(sl.done);
             if (q == cudaErrorNotReady) continue;
             lk.unlock();
@@ -373,6 +428,14 @@ ts_status server_create(const Index *ix, const ts_server_params *prm, Server **o
     s->prm = *prm;
     if (s->prm.max_inflight == 0) s->prm.max_inflight = 2;
     TS_CUDA(cudaGetDevice(&s->device));
+    s->budget = prm->mem_budget_bytes;
+    if (!s->budget) {
+        // three quarters of the device memory free once the pool's unused blocks are returned
+        pool_trim();
+        size_t free_b = 0, total_b = 0;
+        TS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        s->budget = free_b / 4 * 3;
+    }
     s->slots.resize(s->prm.max_inflight);
     ts_batch_params bp;
     memset(&bp, 0, sizeof(bp));
@@ -380,10 +443,14 @@ ts_status server_create(const Index *ix, const ts_server_params *prm, Server **o
     bp.max_queries = prm->max_batch_queries;
     bp.tile_records = prm->tile_records;
     bp.use_graph = prm->use_graph;
-    bp.scratch_rows = prm->scratch_rows ? prm->scratch_rows : SCRATCH_MAX;
+    // hits a batch's count pass keeps: an eighth of the budget per plan (32 B per hit)
+    bp.scratch_rows = prm->scratch_rows
+                          ? prm->scratch_rows
+                          : std::max<uint64_t>(1ull << 20, s->budget / 8 / 32);
     for (Slot &sl : s->slots) {
         // the plans run up to the row scan; every batch's rows are allocated at its exact size
         ts_status st = create_plan(ix, &bp, nullptr, false, &sl.plan);
+        if (st == TS_OK) s->plan_bytes += sl.plan->dbytes;
         if (st == TS_OK) {
             cudaError_t e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
             if (e != cudaSuccess) st = cuda_status(e, "cudaEventCreate(server)");
@@ -466,7 +533,7 @@ ts_status server_wait(Server *s, uint64_t ticket, uint32_t timeout_ms, SearchOut
         timing->start_us = r->start_us;
         timing->done_us = r->done_us;
         timing->batch_requests = r->batch_requests;
-        timing->reserved = 0;
+        timing->requeued = r->requeued;
     }
     const ts_status st = r->status;
     if (st == TS_OK) {
@@ -478,6 +545,17 @@ ts_status server_wait(Server *s, uint64_t ticket, uint32_t timeout_ms, SearchOut
     }
     delete r;
     return st;
+}
+
+void server_info(Server *s, uint64_t *budget, uint64_t *plan_bytes, uint64_t *held_bytes)
+{
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (budget) *budget = s->budget;
+    if (plan_bytes) *plan_bytes = s->plan_bytes;
+    if (held_bytes) {
+        const int64_t h = s->held->load();
+        *held_bytes = h > 0 ? (uint64_t)h : 0;
+    }
 }
 
 ts_status server_cancel(Server *s, uint64_t ticket)

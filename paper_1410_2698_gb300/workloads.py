@@ -194,16 +194,18 @@ def _isotropic(rng, n):
 
 
 def merger_like(seed_offset: int = 0, n_per_cluster: int = 50000, n_samples: int = 201,
-                n_query_traj: int = 2000) -> Workload:
+                n_query_traj: int = 2000, query_seed_offset=None) -> Workload:
     """Merger-like (stand-in for the Merger dataset, Sec. 5.1, which is not available): two
     Plummer spheres of 50,000 particles each (scale radius a = 10, radii truncated at 10a by
     rejection, isotropic directions), centred at (-100,-5,0) and (+100,+5,0) and moving at
     +(0.5,0,0) and -(0.5,0,0) (approaching at relative speed 1 on lines offset by 10 in y). Each
     particle follows x_{k+1} = x_k + v_bulk*dt + N(0, 0.1^2) per axis; 201 samples at dt = 1 on
     t in [0,200] (20,000,000 segments). Queries: 2,000 trajectories, 1,000 per cluster, drawn
-    among the particles whose initial radius is below a. d in {1, 5}."""
+    among the particles whose initial radius is below a (another draw of them with
+    query_seed_offset, the same database). d in {1, 5}."""
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + 3 + seed_offset))
-    qrng = np.random.Generator(np.random.PCG64(SEED_BASE + 3 + 1000 + seed_offset))
+    qoff = seed_offset if query_seed_offset is None else query_seed_offset
+    qrng = np.random.Generator(np.random.PCG64(SEED_BASE + 3 + 1000 + qoff))
     a = 10.0
     centres = np.array([[-100.0, -5.0, 0.0], [100.0, 5.0, 0.0]])
     vbulk = np.array([[0.5, 0.0, 0.0], [-0.5, 0.0, 0.0]])

@@ -116,13 +116,16 @@ def test_plan_runs_equal_plain(use_graph):
 
 @pytest.mark.parametrize("kind", ["temporal", "spatial"])
 def test_plan_rows_equal_with_and_without_scratch(kind):
-    """The count pass keeps its hits for placement after the scan; with a scratch too small for
-    them the write pass sweeps the tiles again. Both give the same rows in the same order."""
+    """The count pass keeps its hits for placement after the scan; the tiles with hits that a
+    too small scratch could not keep are swept again by the write pass. Every scratch size (all
+    hits kept, one, a few, half, all but one) gives the same rows in the same order."""
     w = workloads.tiny()
     idx = api.ts_build_index(w.db, kind=kind)
     reqs = [(w.queries, d, 0.0, 70.0) for d in (1.0, 5.0)]
     out = []
-    for scratch in (0, 8):
+    sizes = [0]
+    while sizes:
+        scratch = sizes.pop(0)
         plan = api.BatchPlan(idx, max_requests=2, max_queries=4000, max_rows=400000,
                              max_units=1 << 20, use_graph=True, scratch_rows=scratch)
         plan.run(reqs)
@@ -131,8 +134,12 @@ def test_plan_rows_equal_with_and_without_scratch(kind):
         assert st["rows"] > 8
         out.append([plan.request_to_host(r) for r in range(len(reqs))])
         plan.free()
-    for a, b in zip(*out):
-        _same(a, b)  # unsorted: the same row order
+        if scratch == 0:
+            n = st["rows"]
+            sizes = [1, 8, n // 2, n - 1]
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            _same(a, b)  # unsorted: the same row order
     for r, req in enumerate(reqs):
         b = out[0][r]
         order = np.lexsort((b["e_idx"], b["q_idx"]))

@@ -61,13 +61,25 @@ def test_tiny_config_matches_oracle(tiny, kind, kw):
         assert stats["n_tests"] == stats["n_qsegs"] * tiny.db.n
 
 
-def test_results_are_bit_identical_to_the_oracle_when_no_pair_is_near_tangent(tiny):
+def test_well_conditioned_intervals_agree_with_the_oracle_to_rounding(tiny):
+    """The kernel's evaluation (fused multiply-adds, refined reciprocal and square root) differs
+    from the oracle's plain one only in rounding: for every pair whose minimum separation is not
+    within 1e-6 * d of d (roots far from coalescing), both interval ends agree to 1e-11 of the
+    pair's overlap, a hundred times inside the acceptance tolerance."""
     d = 5.0
     ref = oracle.search(tiny.db, tiny.queries, tiny.t_start, tiny.t_end, d)
     got, _, _ = _run(tiny.db, tiny.queries, "temporal", d, tiny.t_start, tiny.t_end)
-    diag = parity.compare(got, ref, tiny.db, tiny.queries, tiny.t_start, tiny.t_end, d)
-    if diag["exempt"] == 0:
-        assert diag["bit_exact"]
+    parity.compare(got, ref, tiny.db, tiny.queries, tiny.t_start, tiny.t_end, d)
+    kg = (got["q_idx"].astype(np.int64) << 32) | got["e_idx"].astype(np.int64)
+    kr = (ref["q_idx"].astype(np.int64) << 32) | ref["e_idx"].astype(np.int64)
+    common, ig, ir = np.intersect1d(kg, kr, return_indices=True)
+    well = np.abs(ref["s_min"][ir] - d) > 1e-6 * d
+    assert well.sum() > 1000
+    T = parity.overlap_duration(tiny.db, tiny.queries, ref["q_idx"][ir].astype(np.int64),
+                                ref["e_idx"][ir].astype(np.int64), tiny.t_start, tiny.t_end)
+    e_in = np.abs(got["t_in"][ig] - ref["t_in"][ir])[well] / T[well]
+    e_out = np.abs(got["t_out"][ig] - ref["t_out"][ir])[well] / T[well]
+    assert e_in.max() <= 1e-11 and e_out.max() <= 1e-11, (e_in.max(), e_out.max())
 
 
 def test_deterministic_order(tiny):

@@ -1,12 +1,16 @@
 """Served search: requests from several threads through the request loop; each result must equal
-the same request searched alone (plain ts_search), whatever batch it shared."""
+the same request searched alone (plain ts_search), whatever batch it shared, and the oracle's
+result for that request under the acceptance rule."""
 import threading
+import time
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1410_2698_gb300 import api, workloads
 from paper_1410_2698_gb300.workloads import Segments
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 
@@ -58,8 +62,10 @@ def test_served_results_equal_alone(kind, use_graph):
         assert tm["submit_us"] <= tm["start_us"] <= tm["done_us"]
         batch_sizes.append(tm["batch_requests"])
         q, d, ts, te = req
+        got = res.to_host(sort=True)
         alone = api.ts_search(idx, q, d, ts, te).to_host(sort=True)
-        _same(res.to_host(sort=True), alone)
+        _same(got, alone)
+        parity.compare(got, oracle.search(w.db, q, ts, te, d), w.db, q, ts, te, d)
         res.free()
     srv.close()
     assert max(batch_sizes) > 1  # requests did share batches
@@ -116,4 +122,40 @@ def test_server_wait_is_bounded_and_cancel_works():
         assert e.value.status == 6
     else:
         srv.wait(tickets[-1])[0].free()
+    srv.close()
+
+
+def test_server_defers_a_batch_until_results_release_memory():
+    """Admission by memory: with a budget that holds the plans and one request's rows but not
+    two, a second request waits (its wait times out, the request is not failed) while the first
+    result is held, and completes -- equal to the oracle -- once that result is released."""
+    w = workloads.tiny()
+    idx = api.ts_build_index(w.db, kind="temporal")
+    reqs = [(w.queries, 25.0, 0.0, 70.0), (w.queries.take(np.arange(1500)), 20.0, 0.0, 70.0)]
+    rows = [api.ts_search(idx, q, d, ts, te).count for q, d, ts, te in reqs]
+    kw = dict(max_batch_requests=1, max_batch_queries=4000, max_batch_rows=1 << 26,
+              max_inflight=1, linger_us=0, scratch_rows=1 << 16)
+    probe = api.Server(idx, mem_budget_bytes=1 << 40, **kw)
+    plan_bytes = probe.info()["plan_bytes"]
+    probe.close()
+    assert plan_bytes > 0
+    budget = plan_bytes + 24 * max(rows) + 24 * min(rows) // 2  # one request's rows, not two
+    srv = api.Server(idx, mem_budget_bytes=budget, **kw)
+    assert srv.info()["budget_bytes"] == budget
+    t0 = srv.submit(*reqs[0])
+    res0, tm0 = srv.wait(t0, timeout_ms=60000)
+    assert res0.count == rows[0]
+    assert srv.info()["held_bytes"] == 24 * rows[0]
+    t1 = srv.submit(*reqs[1])
+    with pytest.raises(api.TsError) as e:  # deferred: the budget is held by the first result
+        srv.wait(t1, timeout_ms=1500)
+    assert e.value.status == 5
+    res0.free()
+    res1, tm1 = srv.wait(t1, timeout_ms=60000)
+    q, d, ts, te = reqs[1]
+    got = res1.to_host(sort=True)
+    parity.compare(got, oracle.search(w.db, q, ts, te, d), w.db, q, ts, te, d)
+    assert tm1["done_us"] - tm1["submit_us"] >= 1.0e6  # it waited for the release
+    res1.free()
+    assert srv.info()["held_bytes"] == 0
     srv.close()

@@ -162,7 +162,7 @@ def test_merger_like_sampled(merger, merger_indexes, d):
 
 def test_served_on_merger_like_equals_alone(merger, merger_indexes):
     """Served requests on the resident merger-like database (small runs of core trajectories,
-    own intervals and d) equal the same requests searched alone; one against the oracle."""
+    own intervals and d) equal the same requests searched alone, and the oracle's rows."""
     w = merger
     rng = np.random.default_rng(23)
     seg_per = w.queries.n // len(w.query_traj_ids)
@@ -186,8 +186,49 @@ def test_served_on_merger_like_equals_alone(merger, merger_indexes):
         alone = api.ts_search(index, q, d, ts, te).to_host(sort=True)
         for key in ("q_idx", "e_idx", "t_in", "t_out"):
             assert np.array_equal(got[key], alone[key]), key
+        parity.compare(got, oracle.search(w.db, q, ts, te, d), w.db, q, ts, te, d)
         res.free()
     srv.close()
-    q, d, ts, te = reqs[0]
-    got = api.ts_search(index, q, d, ts, te).to_host(sort=True)
-    parity.compare(got, oracle.search(w.db, q, ts, te, d), w.db, q, ts, te, d)
+
+
+def test_served_stream_shaped_requests_on_merger_like_match_the_oracle(merger, merger_indexes):
+    """Requests shaped like the served stream (the stream generator itself: 1-5,000 query
+    trajectories, log-uniform, each a random database trajectory cut to a run of 10-200
+    segments; the runs' span as interval; d log-uniform in [0.5, 10]) through two servers on the
+    resident merger-like database, every result against the oracle. The generator's first
+    requests are kept while their query segments total at most 30,000 (larger ones are skipped,
+    so the oracle stays within a minute). One server's row limit is one more than the largest
+    request's rows, so batches of several requests are split; the other (temporal index, small
+    tiles) starts with plans whose tile capacity the requests outgrow, so its plans grow. Each
+    mechanism must have re-queued some batch."""
+    w = merger
+    stream = workloads.served_stream(w, n_requests=60, rate_per_s=1.0, seed_offset=5,
+                                     max_traj=5000)
+    reqs, total = [], 0
+    for r in stream:
+        if total + r.queries.n <= 30000:
+            reqs.append(r)
+            total += r.queries.n
+    assert len(reqs) >= 8 and max(r.queries.n for r in reqs) >= 2000
+    st_index = merger_indexes["spatiotemporal"]
+    rows = [api.ts_search(st_index, r.queries, r.d, r.t_start, r.t_end).count for r in reqs]
+    refs = [oracle.search(w.db, r.queries, r.t_start, r.t_end, r.d) for r in reqs]
+    servers = [
+        ("split", api.Server(st_index, max_batch_requests=8, max_batch_queries=1 << 17,
+                             max_batch_rows=max(rows) + 1, max_inflight=2, linger_us=2000)),
+        ("grow", api.Server(merger_indexes["temporal"], max_batch_requests=8,
+                            max_batch_queries=1 << 15, max_batch_rows=1 << 30, max_inflight=2,
+                            tile_records=64, linger_us=2000)),
+    ]
+    for name, srv in servers:
+        tickets = [srv.submit(r.queries, r.d, r.t_start, r.t_end) for r in reqs]
+        requeued = 0
+        for t, r, n, ref in zip(tickets, reqs, rows, refs):
+            res, tm = srv.wait(t, timeout_ms=300000)
+            requeued += tm["requeued"]
+            assert res.count == n
+            got = res.to_host(sort=True)
+            parity.compare(got, ref, w.db, r.queries, r.t_start, r.t_end, r.d)
+            res.free()
+        srv.close()
+        assert requeued > 0, name
