@@ -29,23 +29,41 @@ def test_prepared_requests_point_at_the_callers_columns():
         assert p.max_results == (mr[0] if mr else 0)
 
 
-def test_roofline_picks_the_slower_pipe_against_derived_peaks():
-    # FP32-dominated: 1e9 candidates x 20 flops in 1 ms = 20 TFLOP/s of the FP32 bound
-    r = bench.roofline({"n_tests": 1e9, "n_exact": 1e3, "n_hits": 1e2}, 1.0,
-                       {"fp32_tflops": 78.5, "fp64_tflops": 1.057})
-    assert r["bound"] == "alu" and r["pipe"].startswith("fp32")
-    assert abs(r["achieved"] - 20.0) < 1e-9
-    assert abs(r["peak"] - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
-    assert abs(r["frac"] - 20.0 / r["peak"]) < 1e-12
-    assert abs(r["frac_of_measured"] - 20.0 / 78.5) < 1e-12
-    # FP64-dominated: 1e9 exact tests x 41 + 5e8 hits x 10 flops in 100 ms
-    r = bench.roofline({"n_tests": 1e9, "n_exact": 1e9, "n_hits": 5e8}, 100.0, None)
-    assert r["pipe"].startswith("fp64") and r["peak"] == 1.25
-    assert abs(r["achieved"] - (41e9 + 5e9) / 0.1 / 1e12) < 1e-9
-    assert "measured_peak" not in r
+def test_roofline_picks_the_busier_pipe_from_the_profile(monkeypatch):
+    dev = {"sms": 152, "sm_max_mhz": 2070.0, "name": "GB300"}
+    peaks = {"fp32_tflops": 78.5, "fp64_tflops": 1.057}
+    fp64_peak = 1.057e12 / 2  # DFMA thread-instructions per second
+    issue_peak = 152 * 4 * 2070e6  # warp instructions per second
+    # without a capture of the current sources: no pipe fractions, the algorithmic figure only
+    monkeypatch.setattr(bench, "PAIR_PROFILE", {})
+    r = bench.roofline({"n_tests": 1e9, "n_exact": 1e8, "n_hits": 5e7}, 100.0, peaks, "w", dev)
+    assert r["frac"] is None and r["bound"] == "alu"
+    alg = (41 * 1e8 + 10 * 5e7) / 0.1 / 1e12
+    assert abs(r["algorithmic_fp64"]["achieved_tflops"] - alg) < 1e-12
+    assert abs(r["algorithmic_fp64"]["frac"] - alg / 1.057) < 1e-12
+    # FP64-dominated: 1e8 exact tests x 60 FP64 instructions in 100 ms
+    prof = {"fp64_inst_per_exact": 60.0, "warp_inst_per_test": 0.5, "hit_ratio": 0.5,
+            "dram_bytes_per_test": 0.25, "capture": "profiles/x.md",
+            "sources": bench.pair_source_hash()}
+    monkeypatch.setattr(bench, "PAIR_PROFILE", {"w": prof})
+    tot = {"n_tests": 1e9, "n_exact": 1e8, "n_hits": 5e7, "launches": 2}
+    r = bench.roofline(tot, 100.0, peaks, "w", dev)
+    assert r["pipe"] == "fp64"
+    assert abs(r["frac"] - 60 * 1e8 / 0.1 / fp64_peak) < 1e-12
+    assert abs(r["pipes"]["issue"]["frac"] - 0.5 * 1e9 / 0.1 / issue_peak) < 1e-12
+    assert abs(r["achieved"] * 1e9 - 60 * 1e8 / 0.1) < 1e-3
+    assert r["traffic"] == 0.25 * 1e9 / 2
+    # issue-dominated: many candidates, few exact tests
+    tot = {"n_tests": 1e11, "n_exact": 1e6, "n_hits": 1e5, "launches": 2}
+    r = bench.roofline(tot, 100.0, peaks, "w", dev)
+    assert r["pipe"] == "issue"
+    assert abs(r["frac"] - 0.5 * 1e11 / 0.1 / issue_peak) < 1e-12
+    # a profile of other sources is not used
+    monkeypatch.setattr(bench, "PAIR_PROFILE", {"w": dict(prof, sources="0" * 16)})
+    assert bench.roofline(tot, 100.0, peaks, "w", dev)["frac"] is None
 
 
-def test_traffic_figure_is_keyed_to_the_pair_kernel_sources(tmp_path):
+def test_profile_figures_are_keyed_to_the_pair_kernel_sources(tmp_path):
     csrc = os.path.join(ROOT, "paper_1410_2698_gb300", "csrc")
     h = bench.pair_source_hash()
     assert h == bench.pair_source_hash(csrc) and len(h) == 16
