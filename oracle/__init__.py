@@ -2,7 +2,8 @@
 
 Plain FP64 C (``ts_oracle.c``) behind ctypes. Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package; the product library never does. The
-oracle and the CUDA path share no code.
+oracle and the CUDA path share no code. ``ts_rtree.c`` (class ``RTree``) is the CPU R-tree
+baseline of the benchmark, built into the same library and using the oracle's pair test.
 
 Every function cites the passage of the paper it follows (Gowanlock & Casanova, Sec. 3.1 problem
 definition, Sec. 4.1 flatly structured grid, Sec. 4.2 temporal index, Sec. 4.3 spatiotemporal
@@ -19,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ts_oracle.c")
+_SOURCES = [_SRC, os.path.join(_HERE, "ts_rtree.c"), os.path.join(_HERE, "ts_oracle.h")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libts_oracle.so")
 _lock = threading.Lock()
@@ -35,11 +37,11 @@ def build(force: bool = False) -> str:
     baseline). Returns the library path."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SOURCES)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
+           "-fno-fast-math", "-Wall", "-o", tmp, _SRC, _SOURCES[1], "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -59,6 +61,17 @@ def _load():
             lib.orc_search_mt.argtypes = [_I64, _P, _I64, _P, _D, _D, _D, _I32, _P, _I32, _P, _P,
                                           _P, _P, _P, _P]
             lib.orc_search_mt.restype = _I64
+            lib.orc_rtree_build.argtypes = [_I64, _P, _I32]
+            lib.orc_rtree_build.restype = _P
+            lib.orc_rtree_free.argtypes = [_P]
+            lib.orc_rtree_free.restype = None
+            lib.orc_rtree_shape.argtypes = [_P, _P, _P]
+            lib.orc_rtree_shape.restype = None
+            lib.orc_rtree_count.argtypes = [_P, _I64, _P, _D, _D, _D, _I32, _P, _P]
+            lib.orc_rtree_count.restype = _I64
+            lib.orc_rtree_search.argtypes = [_P, _I64, _P, _D, _D, _D, _I32, _I64, _P, _P, _P,
+                                             _P]
+            lib.orc_rtree_search.restype = _I64
             lib.orc_openmp_max_threads.argtypes = []
             lib.orc_openmp_max_threads.restype = _I32
             lib.orc_temporal_index.argtypes = [_I64, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P]
@@ -367,3 +380,64 @@ def grid1_candidates(g, lo3, w3, longest3, off, qmin3, qmax3, w0, w1, d):
     lib.orc_grid1_candidates(g, _ptr(lo), _ptr(w), _ptr(L), _ptr(off), nq, ctypes.cast(qa, _P),
                              ctypes.cast(qb, _P), _ptr(w0), _ptr(w1), d, _ptr(runs), _ptr(cand))
     return runs, cand
+
+
+class RTree:
+    """CPU in-memory R-tree over a database (the paper's CPU comparator, Sec. 5): groups of r
+    consecutive segments of a trajectory, one 4-D box per group, bulk-loaded (STR packing);
+    queries on OpenMP threads test the segments of every group whose box meets the query's
+    window and d-widened MBB with the oracle's interaction test. Keeps the database columns
+    alive while it lives."""
+
+    def __init__(self, db, r=1):
+        lib = _load()
+        self._cols = _cols(db)
+        self.r = int(r)
+        self._h = lib.orc_rtree_build(self._cols.n, self._cols.ptr, self.r)
+        if not self._h:
+            raise MemoryError("R-tree build failed")
+
+    def shape(self):
+        ng, nl = np.zeros(1, dtype=np.int64), np.zeros(1, dtype=np.int32)
+        _load().orc_rtree_shape(self._h, _ptr(ng), _ptr(nl))
+        return int(ng[0]), int(nl[0])
+
+    def count(self, queries, t_start, t_end, d, threads=None):
+        """(hits, interaction tests, query segments) on `threads` threads (all by default)."""
+        q = _cols(queries)
+        nt, nq = np.zeros(1, dtype=np.int64), np.zeros(1, dtype=np.int64)
+        threads = max_threads() if threads is None else int(threads)
+        c = _load().orc_rtree_count(self._h, q.n, q.ptr, t_start, t_end, d, threads, _ptr(nt),
+                                    _ptr(nq))
+        return int(c), int(nt[0]), int(nq[0])
+
+    def search(self, queries, t_start, t_end, d, threads=None):
+        """Every hit as arrays q_idx, e_idx, t_in, t_out sorted by (q_idx, e_idx)."""
+        lib = _load()
+        q = _cols(queries)
+        threads = max_threads() if threads is None else int(threads)
+        cap = 1 << 16
+        while True:
+            oq, oe = np.empty(cap, dtype=np.int64), np.empty(cap, dtype=np.int64)
+            ti, to = np.empty(cap), np.empty(cap)
+            n = lib.orc_rtree_search(self._h, q.n, q.ptr, t_start, t_end, d, threads, cap,
+                                     _ptr(oq), _ptr(oe), _ptr(ti), _ptr(to))
+            if n < 0:
+                raise MemoryError("R-tree search failed")
+            if n <= cap:
+                break
+            cap = int(n)
+        order = np.lexsort((oe[:n], oq[:n]))
+        return {"q_idx": oq[:n][order].astype(np.uint32), "e_idx": oe[:n][order].astype(np.uint32),
+                "t_in": ti[:n][order], "t_out": to[:n][order]}
+
+    def free(self):
+        if self._h:
+            _load().orc_rtree_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -22,11 +22,7 @@
 #include <omp.h>
 #endif
 
-/* A segment with its velocity: position p(t) = p0 + v * (t - t0) on [t0, t1] (linear motion
- * between the samples of a trajectory, Sec. 3.1). */
-typedef struct {
-    double x0, y0, z0, t0, vx, vy, vz, t1;
-} orc_seg;
+#include "ts_oracle.h"
 
 static void seg_load(const double *const *f, int64_t i, orc_seg *s)
 {
@@ -40,6 +36,8 @@ static void seg_load(const double *const *f, int64_t i, orc_seg *s)
     s->vy = (f[5][i] - f[1][i]) / dt;
     s->vz = (f[6][i] - f[2][i]) / dt;
 }
+
+void orc_seg_load(const double *const *f, int64_t i, orc_seg *s) { seg_load(f, i, s); }
 
 static double dmax(double a, double b) { return a > b ? a : b; }
 

@@ -323,3 +323,27 @@ def test_sweep_counters_are_consistent(tiny, kind):
     assert st["n_hits"] <= st["n_exact"] <= st["n_tests"]
     res.free()
     idx.free()
+
+
+def test_st_schedule_widens_an_expanded_extent_that_lands_on_a_boundary():
+    """The same hand case as the oracle's pin: subbins of width 10 from 0 in every dimension
+    (entries spanning [0, 40], four subbins); a query at y = z = 20 with d = 2 meets two subbins
+    in y and in z. Query A (x in [12, 12.5]) has its d-expanded x extent start exactly at the
+    boundary 10: the relative widening makes it meet [0,10) too, so the temporal range serves it
+    (selector 3, all seven entries). Query B (x from 12.5) meets only [10,20): the x subbin serves
+    it, one entry (x = 15)."""
+    pts = [(0, 0, 0), (40, 40, 40), (5, 20, 20), (9.5, 20, 20), (15, 20, 20), (25, 20, 20),
+           (35, 20, 20)]
+    db = segset([seg(p, 0, p, 1) for p in pts])
+    q = segset([seg((12, 20, 20), 0, (12.5, 20, 20), 1), seg((12.5, 20, 20), 0, (13, 20, 20), 1)])
+    idx = api.ts_build_index(db, kind="spatiotemporal", t_bins=1, sub_bins=4)
+    info = idx.info()
+    assert list(info["sub_bins"]) == [4, 4, 4]
+    assert list(info["sub_lo"]) == [0.0, 0.0, 0.0] and list(info["sub_w"]) == [10.0, 10.0, 10.0]
+    sel, lo, hi = api.ts_schedule(idx, q, 2.0, 0.0, 1.0)
+    assert sel[0] == 3 and hi[0] - lo[0] == 7
+    assert sel[1] == 0 and hi[1] - lo[1] == 1
+    got = api.ts_search(idx, q, 2.0, 0.0, 1.0).to_host(sort=True)
+    ref = oracle.search(db, q, 0.0, 1.0, 2.0)
+    parity.compare(got, ref, db, q, 0.0, 1.0, 2.0)
+    idx.free()

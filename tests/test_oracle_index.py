@@ -209,3 +209,30 @@ def test_one_cell_grid_candidates_cover_every_hit():
             a = (qmin[k][qi] - d) - longest[k]
             b = qmax[k][qi] + d
             assert lo[k] + c[k] * w[k] <= b and (c[k] == g - 1 or lo[k] + (c[k] + 1) * w[k] > a)
+
+
+def test_st_schedule_widens_an_expanded_extent_that_lands_on_a_boundary():
+    # x subbins [0,10), [10,20), [20,30), [30,inf) (lo 0, width 10); y and z subbins of width 1,
+    # so a query with d = 2 meets at least four of them there and only x can serve it.
+    # Query A: x in [12, 12.5]: the d-expanded extent starts exactly at the boundary 10, the
+    # relative widening of the extent (reading: a relative 1e-12, against the rounding of
+    # min - d) makes it meet [0,10) as well as [10,20): two subbins, so the temporal range
+    # serves it (selector 3). Query B: x in [12.5, 13] starts at 10.5, inside [10,20) only: the
+    # x subbin serves it (selector 0) with the ids of subbin 1 in bin 0.
+    xs = np.array([5.0, 9.5, 15.0, 25.0, 35.0])
+    emin = np.stack([xs, np.full(5, 20.0), np.full(5, 20.0)], axis=1)
+    emax = emin.copy()
+    bin_of = np.zeros(5, dtype=np.int32)
+    tidx = {"bin_start": np.array([0.0]), "bin_end": np.array([1.0]),
+            "bin_off": np.array([0, 5], dtype=np.int64)}
+    dims = []
+    for dim, (w, v) in enumerate([(10.0, 4), (1.0, 40), (1.0, 40)]):
+        ids, off = oracle.st_dim(emin[:, dim], emax[:, dim], bin_of, 1, 0.0, w, v)
+        dims.append({"lo": 0.0, "w": w, "v": v, "off": off, "ids": ids})
+    qmin = [np.array([12.0, 12.5]), np.array([20.0, 20.0]), np.array([20.0, 20.0])]
+    qmax = [np.array([12.5, 13.0]), np.array([20.0, 20.0]), np.array([20.0, 20.0])]
+    w0, w1 = np.array([0.0, 0.0]), np.array([1.0, 1.0])
+    sel, lo, hi = oracle.st_schedule(tidx, dims, qmin, qmax, w0, w1, 2.0)
+    assert sel[0] == 3 and (lo[0], hi[0]) == (0, 5)
+    assert sel[1] == 0
+    np.testing.assert_array_equal(dims[0]["ids"][lo[1]:hi[1]], [2])  # the entry at x = 15
