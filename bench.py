@@ -657,7 +657,7 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
     reqs = api.prepare_requests([(qhost, d, w.t_start, w.t_end) for d in w.distances])
     rows_out, keep = _pinned_rows(max_rows)
     if make_plan is not None:
-        total_ms, h2d, d2h, qsegs = 0.0, 0, 0, 0
+        total_ms, copy_ms, h2d, d2h, qsegs = 0.0, 0.0, 0, 0, 0
         steps = max(1, min(args.steps, 5))
         for k in kinds:
             plan = make_plan(k, False)
@@ -668,16 +668,21 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
                 t0 = time.perf_counter()
                 plan.run(reqs)
                 st = plan.wait()
+                t1 = time.perf_counter()
                 rows, _ = plan.rows_to_host(out=rows_out)  # every request's rows, one copy
                 d2h += sum(v.nbytes for v in rows.values())
                 torch.cuda.synchronize()
-                total_ms += (time.perf_counter() - t0) * 1e3
+                t2 = time.perf_counter()
+                total_ms += (t2 - t0) * 1e3
+                copy_ms += (t2 - t1) * 1e3
                 qsegs += st["stats"]["n_qsegs"]
                 h2d += 8 * 8 * w.queries.n * reqs.n
             plan.free()
         return {"value": qsegs / (total_ms / 1e3), "unit": "query segs/s",
                 "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
-                "steps": steps, "host_buffers": "pinned"}
+                "steps": steps, "host_buffers": "pinned",
+                "rows_copy_ms_per_step": copy_ms / steps,
+                "rows_copy_gbs": d2h / (copy_ms / 1e3) / 1e9 if copy_ms else None}
     ms = []
     h2d = d2h = qsegs = 0
     for s in range(args.steps + 1):
@@ -738,6 +743,35 @@ def run_served(args, api, w, index, tile=0):
         lat_plain.append((time.perf_counter() - a) * 1e3)
     plain_s = time.perf_counter() - t0
     mu_plain = len(stream) / plain_s
+
+    def plain_arrivals(arrivals):
+        """One plain search per request in arrival order on one worker (a FIFO server of plain
+        launches): latency = completion - arrival, queueing included."""
+        import queue
+        qu = queue.Queue()
+        lat = [0.0] * len(stream)
+        start = time.perf_counter()
+
+        def worker():
+            while True:
+                item = qu.get()
+                if item is None:
+                    return
+                i, t_arr = item
+                r = stream[i]
+                api.ts_search(index, r.queries, r.d, r.t_start, r.t_end).free()
+                lat[i] = (time.perf_counter() - t_arr) * 1e3
+
+        th = threading.Thread(target=worker)
+        th.start()
+        for i in range(len(stream)):
+            dt = start + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            qu.put((i, start + arrivals[i]))
+        qu.put(None)
+        th.join()
+        return time.perf_counter() - start, lat
     srv = api.Server(index, max_batch_requests=64, max_batch_queries=max(1 << 20, 2 * max_q),
                      max_batch_rows=max(1 << 25, 2 * max_rows), max_inflight=2, use_graph=True,
                      linger_us=200, tile_records=tile)
@@ -778,10 +812,15 @@ def run_served(args, api, w, index, tile=0):
             poi_s, lat_poi, rows_poi, sizes_poi = serve(arrivals)
             if rows_poi != rows_plain:
                 raise RuntimeError("served and plain forms disagree on the result count")
+            pl_s, lat_pl = plain_arrivals(arrivals)
             poisson.append({"rho": rho, "arrival_rate_req_s": lam,
                             "qsegs_per_s": qsegs / poi_s, "p50_ms": _pct(lat_poi, 50),
                             "p99_ms": _pct(lat_poi, 99),
-                            "mean_batch_requests": float(np.mean(sizes_poi))})
+                            "mean_batch_requests": float(np.mean(sizes_poi)),
+                            "plain": {"qsegs_per_s": qsegs / pl_s, "p50_ms": _pct(lat_pl, 50),
+                                      "p99_ms": _pct(lat_pl, 99),
+                                      "form": "the same arrivals, one plain search per request "
+                                              "in arrival order (queueing included)"}})
     finally:
         srv.close()
     if rows_plain != rows_sat:
