@@ -33,13 +33,19 @@ sys.path.insert(0, ROOT)
 METRIC = "seg-pair tests/s & query segs/s, plain vs batched/served; p50/p99 latency"
 EXACT_FLOPS = 41     # FP64 flops per exact test of the definition (window, positions, a, b, c, decision)
 INTERVAL_FLOPS = 10  # FP64 flops per hit for the roots (sqrt, 2 div, clamps; sqrt and div as 1 each)
-# Per-unit counts of the pair kernel from one ncu capture of the same kernel sources (hash
+# Per-unit counts of the pair kernel from ncu captures of the same kernel sources (hash
 # `sources`; a profile of other sources is not used): per exact FP64 test, the FP64-pipe thread
-# instructions (smsp__inst_executed_pipe_fp64.sum x 32 / exact tests: the exact tests run on full
-# warps) at the capture's hits per exact test (`hit_ratio`); per candidate test, the warp
-# instructions issued (smsp__inst_executed.sum / tests); per launch, DRAM bytes
-# (dram__bytes_read.sum + dram__bytes_write.sum) per candidate test.
-PAIR_PROFILE = {}
+# instructions (sm__thread_inst_executed_pipe_fp64_pred_on.sum / exact tests) at the capture's
+# hits per exact test (`hit_ratio`); per candidate test, the warp instructions issued
+# (smsp__inst_executed.sum / tests); per exact test, DRAM bytes (dram__bytes_read.sum +
+# dram__bytes_write.sum; the gathered FP64 records and the kept hits). The merger-like workload at
+# a tenth of the particles (merger-like-2m) stands in for the full one, whose launches are too
+# large to capture: the per-unit counts are those of the same kernel at the same hit ratio.
+_MERGER_PROFILE = {"fp64_inst_per_exact": 58.447, "warp_inst_per_test": 0.62752,
+                   "dram_bytes_per_exact": 62.06, "hit_ratio": 0.8697,
+                   "capture": "profiles/k_pair_merger-like-2m_count-pass.md",
+                   "sources": "b91bf21201c170ab"}
+PAIR_PROFILE = {"merger-like-20m": _MERGER_PROFILE, "merger-like-2m": _MERGER_PROFILE}
 PAIR_SOURCES = ("ts_search.cuh", "ts_internal.cuh", "ts_device.cuh")
 
 
@@ -263,11 +269,17 @@ def roofline(tot, pair_ms, peaks, workload, dev_info):
                 "pipes": pipes,
                 "hit_ratio": tot["n_hits"] / max(tot["n_exact"], 1),
                 "profile_hit_ratio": prof.get("hit_ratio")})
-    if prof.get("dram_bytes_per_test") is not None:
+    if prof.get("dram_bytes_per_exact") is not None:
         launches = max(tot.get("launches", 1), 1)
-        out["traffic"] = prof["dram_bytes_per_test"] * tot["n_tests"] / launches
-        out["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled "
-                               "from the capture by the candidate tests of this step's launches")
+        out["traffic"] = prof["dram_bytes_per_exact"] * tot["n_exact"] / launches
+        out["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per count-pass "
+                               "launch (the write passes sweep no tile when every hit was kept), "
+                               "scaled from the capture by this step's exact tests")
+        out["algorithmic_bytes"] = {
+            "per_exact_test": 64 + 80, "per_hit": 32 + 24,
+            "note": "the entry's and the query's FP64 records per exact test (gathered, mostly "
+                    "from L2) and a kept hit plus its row per hit; records read by the FP32 "
+                    "sweep (32 B, shared by up to 32 queries) not counted"}
     return out
 
 
@@ -531,7 +543,7 @@ def run_gpu(args):
     # at a time these are the timed headline step's own events; with overlapped plans (where a
     # plan's events also span the other plans' kernels) a loop of the same plans one at a time.
     step_tot = {k: v / n_alone for k, v in atot.items()}  # per step
-    step_tot["launches"] = 2 * len(kinds)  # count + write pass of every plan
+    step_tot["launches"] = len(kinds)  # count passes (one per plan)
     roof = roofline(step_tot, apair_ms / n_alone, peaks, w.name, dinfo)
     if serial:
         roof["timed_form"] = ("batched, the timed headline step itself (plans one at a time; "

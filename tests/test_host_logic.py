@@ -43,7 +43,7 @@ def test_roofline_picks_the_busier_pipe_from_the_profile(monkeypatch):
     assert abs(r["algorithmic_fp64"]["frac"] - alg / 1.057) < 1e-12
     # FP64-dominated: 1e8 exact tests x 60 FP64 instructions in 100 ms
     prof = {"fp64_inst_per_exact": 60.0, "warp_inst_per_test": 0.5, "hit_ratio": 0.5,
-            "dram_bytes_per_test": 0.25, "capture": "profiles/x.md",
+            "dram_bytes_per_exact": 100.0, "capture": "profiles/x.md",
             "sources": bench.pair_source_hash()}
     monkeypatch.setattr(bench, "PAIR_PROFILE", {"w": prof})
     tot = {"n_tests": 1e9, "n_exact": 1e8, "n_hits": 5e7, "launches": 2}
@@ -52,7 +52,7 @@ def test_roofline_picks_the_busier_pipe_from_the_profile(monkeypatch):
     assert abs(r["frac"] - 60 * 1e8 / 0.1 / fp64_peak) < 1e-12
     assert abs(r["pipes"]["issue"]["frac"] - 0.5 * 1e9 / 0.1 / issue_peak) < 1e-12
     assert abs(r["achieved"] * 1e9 - 60 * 1e8 / 0.1) < 1e-3
-    assert r["traffic"] == 0.25 * 1e9 / 2
+    assert r["traffic"] == 100.0 * 1e8 / 2
     # issue-dominated: many candidates, few exact tests
     tot = {"n_tests": 1e11, "n_exact": 1e6, "n_hits": 1e5, "launches": 2}
     r = bench.roofline(tot, 100.0, peaks, "w", dev)
