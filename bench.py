@@ -45,7 +45,14 @@ _MERGER_PROFILE = {"fp64_inst_per_exact": 58.447, "warp_inst_per_test": 0.62752,
                    "dram_bytes_per_exact": 62.06, "hit_ratio": 0.8697,
                    "capture": "profiles/k_pair_merger-like-2m_count-pass.md",
                    "sources": "b91bf21201c170ab"}
-PAIR_PROFILE = {"merger-like-20m": _MERGER_PROFILE, "merger-like-2m": _MERGER_PROFILE}
+# the Random-walk 1M workload (filter-bound: the issue slots bind); its DRAM bytes are mostly the
+# records the sweep streams, scaled here by the exact tests of the same workload
+_RW1M_PROFILE = {"fp64_inst_per_exact": 14.39, "warp_inst_per_test": 0.5490,
+                 "dram_bytes_per_exact": 436.7, "hit_ratio": 0.348,
+                 "capture": "profiles/k_pair_random-walk-1m_count-pass.md",
+                 "sources": "b91bf21201c170ab"}
+PAIR_PROFILE = {"merger-like-20m": _MERGER_PROFILE, "merger-like-2m": _MERGER_PROFILE,
+                "random-walk-1m": _RW1M_PROFILE}
 PAIR_SOURCES = ("ts_search.cuh", "ts_internal.cuh", "ts_device.cuh")
 
 
