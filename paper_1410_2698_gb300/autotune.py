@@ -38,6 +38,23 @@ def signature(db, requests, kind) -> str:
     return h.hexdigest()[:24]
 
 
+def sm_count() -> int:
+    """Streaming multiprocessors of the current device (152 on a GB300)."""
+    try:
+        import torch
+        return int(torch.cuda.get_device_properties(torch.cuda.current_device())
+                   .multi_processor_count)
+    except Exception:  # pragma: no cover
+        return 152
+
+
+def step_grids(sms=None):
+    """Pair-kernel grids the overlapped step is tuned over: all resident blocks (0), then 1.75,
+    1.5, 1.25 and 1 blocks per SM."""
+    sms = sms or sm_count()
+    return (0, (7 * sms) // 4, (3 * sms) // 2, (5 * sms) // 4, sms)
+
+
 def _gpu_name() -> str:
     try:
         import torch
@@ -153,7 +170,7 @@ def tune(db, requests, kind, cache_path=DEFAULT_CACHE, repeats=3, max_rows=1 << 
     units = _units(idx, requests, kind)
     try:
         for tile in TILES:
-            for pb in (0, 152):  # all resident blocks, or one block per SM
+            for pb in (0, sm_count()):  # all resident blocks, or one block per SM
                 t, st = _time_plan(idx, requests, tile, pb, max_rows, repeats, units)
                 if t is not None:
                     trials.append({"params": dict(best[0]), "tile_records": tile,
@@ -193,7 +210,7 @@ def time_overlapped(plans, requests, order, warmup=8, reps=20):
     return time.perf_counter() - t0
 
 
-def tune_overlapped(make_plans, kinds, requests, grids=(0, 266, 228, 190, 152), tune_grid=True,
+def tune_overlapped(make_plans, kinds, requests, grids=None, tune_grid=True,
                     timer=time_overlapped):
     """Tune a step that runs several plans at once (one per kind, overlapping on their streams):
     first the persistent pair kernel's grid shared by the plans (`grids`, 0 = all resident
@@ -201,6 +218,7 @@ def tune_overlapped(make_plans, kinds, requests, grids=(0, 266, 228, 190, 152), 
     plans' kernels), then the order in which the plans are launched. make_plans(pair_blocks)
     returns {kind: plan}; the plans it returns are freed here. Returns (pair_blocks, order)."""
     import itertools
+    grids = step_grids() if grids is None else grids
     pair_blocks = None
     if tune_grid:
         best = None

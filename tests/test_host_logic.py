@@ -124,8 +124,11 @@ def test_overlapped_step_tuning_picks_the_fastest_grid_then_order():
         return grid_cost[pb] + (0.0 if order[0] == "temporal" else 1.0) + 0.1 * order.index(
             "spatial")
 
+    # the grids follow the SM count: all resident, then 1.75 / 1.5 / 1.25 / 1 blocks per SM
+    assert autotune.step_grids(152) == (0, 266, 228, 190, 152)
+    assert autotune.step_grids(148) == (0, 259, 222, 185, 148)
     pb, order = autotune.tune_overlapped(lambda pb: {k: FakePlan(pb) for k in kinds}, kinds,
-                                         None, timer=timer)
+                                         None, grids=autotune.step_grids(152), timer=timer)
     assert pb == 228
     assert order[0] == "temporal" and order == ["temporal", "spatial", "spatiotemporal"]
     assert FakePlan.live == 0  # every plan made for a trial was freed
