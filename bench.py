@@ -677,6 +677,7 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
     rows_out, keep = _pinned_rows(max_rows)
     if make_plan is not None:
         total_ms, copy_ms, h2d, d2h, qsegs = 0.0, 0.0, 0, 0, 0
+        copies = []
         steps = max(1, min(args.steps, 5))
         for k in kinds:
             plan = make_plan(k, False)
@@ -694,6 +695,7 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
                 t2 = time.perf_counter()
                 total_ms += (t2 - t0) * 1e3
                 copy_ms += (t2 - t1) * 1e3
+                copies.append(round((t2 - t1) * 1e3, 1))
                 qsegs += st["stats"]["n_qsegs"]
                 h2d += 8 * 8 * w.queries.n * reqs.n
             plan.free()
@@ -701,7 +703,8 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
                 "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
                 "steps": steps, "host_buffers": "pinned",
                 "rows_copy_ms_per_step": copy_ms / steps,
-                "rows_copy_gbs": d2h / (copy_ms / 1e3) / 1e9 if copy_ms else None}
+                "rows_copy_gbs": d2h / (copy_ms / 1e3) / 1e9 if copy_ms else None,
+                "rows_copy_ms": copies}
     ms = []
     h2d = d2h = qsegs = 0
     for s in range(args.steps + 1):

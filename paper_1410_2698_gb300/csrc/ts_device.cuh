@@ -111,13 +111,35 @@ static __device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e,
     return true;
 }
 
-// Division-free hit decision: the minimum of a tau^2 + 2 b tau + c over [0, T] is <= 0.
+// Sign and order tests of FP64 values made on their bit patterns, so that they run on the integer
+// pipe instead of the FP64 pipe (on GB300 an FP64 instruction costs as much pipe time as 32 integer
+// ones). For values that are not NaN; -0.0 and +0.0 compare equal, as in IEEE arithmetic.
+static __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// x < 0 (sign bit set and not -0.0)
+static __device__ __forceinline__ bool neg(double x)
+{
+    const long long v = dbits(x);
+    return v < 0 && (v << 1) != 0;
+}
+// x <= 0 (a set sign bit as a signed integer is negative; +0.0 is 0)
+static __device__ __forceinline__ bool nonpos(double x) { return dbits(x) <= 0; }
+// x == 0
+static __device__ __forceinline__ bool zero(double x) { return (dbits(x) << 1) == 0; }
+// |x| < |y|: the magnitudes order as their bit patterns without the sign
+static __device__ __forceinline__ bool mag_lt(double x, double y)
+{
+    return (dbits(x) & 0x7fffffffffffffffll) < (dbits(y) & 0x7fffffffffffffffll);
+}
+
+// Division-free hit decision: the minimum of a tau^2 + 2 b tau + c over [0, T] is <= 0 (a >= 0,
+// T > 0). The branch tests are sign and magnitude tests on the integer pipe: a is a sum of
+// squares, and -b and aT are compared only when b < 0.
 static __device__ __forceinline__ bool quad_hit(const Quad &k)
 {
-    if (k.a == 0.0 || k.b >= 0.0) return k.c <= 0.0;        // minimum at tau = 0
+    if (zero(k.a) || !neg(k.b)) return nonpos(k.c);           // minimum at tau = 0
     const double aT = k.a * k.T;
-    if (-k.b >= aT) return fma(aT + 2.0 * k.b, k.T, k.c) <= 0.0;  // at tau = T
-    return fma(k.b, k.b, -(k.a * k.c)) >= 0.0;               // interior minimum
+    if (!mag_lt(k.b, aT)) return nonpos(fma(aT + 2.0 * k.b, k.T, k.c));  // at tau = T (-b >= aT)
+    return !neg(fma(k.b, k.b, -(k.a * k.c)));                  // interior minimum
 }
 
 // |x| within [2^-1000, 2^1000) (its biased exponent, sign ignored): the range where the refined
@@ -141,12 +163,13 @@ static __device__ __forceinline__ double rcp_nr(double x)
 
 // sqrt(x) by Newton-Raphson from the hardware estimate of 1/sqrt(x) (rsqrt.approx.ftz.f64): the
 // coupled iteration on g ~ sqrt(x), h ~ 1/(2 sqrt(x)) (r = 1/2 - g h; g += g r; h += h r), then
-// one Newton correction of g with the residual x - g^2. For x in the nr_range.
+// one Newton correction of g with the residual x - g^2. For x in the nr_range (the estimate is
+// then a normal number, and halving it is a decrement of its exponent, on the integer pipe).
 static __device__ __forceinline__ double sqrt_nr(double x)
 {
     double y;
     asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    double g = x * y, h = 0.5 * y;
+    double g = x * y, h = __longlong_as_double(dbits(y) - (1ll << 52));
     const double r = fma(-g, h, 0.5);
     g = fma(g, r, g);
     h = fma(h, r, h);
@@ -157,28 +180,35 @@ static __device__ __forceinline__ double sqrt_nr(double x)
 // disc = b^2 - a c). The square root and the two quotients come from the refined estimates
 // above (relative error of a few ulps, far inside the 1e-9 interval tolerance); values outside
 // their range take the library's sqrt and division.
+//
+// The roots need no comparison of their values: with s of the sign opposite to b's sign bit,
+// s/a is the smaller root when b's sign bit is clear and the larger when it is set (c/s is the
+// other), and every clamp below compares a value with 0 or two non-negative values, which the
+// integer pipe does on the bit patterns.
 static __device__ __forceinline__ void quad_interval(const Quad &k, double *tin, double *tout)
 {
     double lower, upper;
-    if (k.a == 0.0) {
+    if (zero(k.a)) {
         lower = 0.0;
         upper = k.T;
     } else {
         double disc = fma(k.b, k.b, -(k.a * k.c));
-        if (disc < 0.0) disc = 0.0;  // only reachable within rounding of a tangency
+        if (neg(disc)) disc = 0.0;  // only reachable within rounding of a tangency
         const double sq = nr_range(disc) ? sqrt_nr(disc) : sqrt(disc);
         const double s = -(k.b + copysign(sq, k.b));
         double r1, r2;
-        if (s == 0.0) {
+        if (zero(s)) {
             r1 = 0.0;
             r2 = 0.0;
         } else {
             r1 = nr_range(k.a) ? s * rcp_nr(k.a) : s / k.a;
             r2 = nr_range(s) ? k.c * rcp_nr(s) : k.c / s;
         }
-        lower = dmx(0.0, dmn(r1, r2));
-        upper = dmn(k.T, dmx(r1, r2));
-        if (upper < lower) upper = lower;  // only reachable within rounding of a tangency
+        const bool b_sign = dbits(k.b) < 0;  // sign bit (also for -0.0, as copysign reads it)
+        const double lo = b_sign ? r2 : r1, hi = b_sign ? r1 : r2;
+        lower = neg(lo) ? 0.0 : lo;                               // max(0, lo)
+        upper = (neg(hi) || mag_lt(hi, k.T)) ? hi : k.T;          // min(T, hi)
+        if (neg(upper) || mag_lt(upper, lower)) upper = lower;    // (within rounding only)
     }
     *tin = k.t_lo + lower;
     *tout = k.t_lo + upper;
