@@ -93,11 +93,23 @@ struct Quad {
 
 // Window and quadratic coefficients; false when the common window has no positive length.
 // r0 = p_q(t_lo) - p_l(t_lo), dv = v_q - v_l, a = dv.dv, b = r0.dv, c = r0.r0 - d^2.
+// When the four window bounds have their sign bits clear (non-negative times, the usual case) the
+// window is found on the integer pipe: non-negative doubles order as their bit patterns.
 static __device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e, double dd, Quad &o)
 {
-    const double t_lo = dmx(q.w0, e.t0);
-    const double t_hi = dmn(q.w1, e.t1);
-    if (!(t_lo < t_hi)) return false;
+    double t_lo, t_hi;
+    const long long a0 = __double_as_longlong(q.w0), b0 = __double_as_longlong(e.t0);
+    const long long a1 = __double_as_longlong(q.w1), b1 = __double_as_longlong(e.t1);
+    if ((a0 | b0 | a1 | b1) >= 0) {
+        const long long lo = a0 > b0 ? a0 : b0, hi = a1 < b1 ? a1 : b1;
+        if (!(lo < hi)) return false;
+        t_lo = __longlong_as_double(lo);
+        t_hi = __longlong_as_double(hi);
+    } else {
+        t_lo = dmx(q.w0, e.t0);
+        t_hi = dmn(q.w1, e.t1);
+        if (!(t_lo < t_hi)) return false;
+    }
     const double dq = t_lo - q.t0, de = t_lo - e.t0;
     const double rx = fma(q.vx, dq, q.x0) - fma(e.vx, de, e.x0);
     const double ry = fma(q.vy, dq, q.y0) - fma(e.vy, de, e.y0);
