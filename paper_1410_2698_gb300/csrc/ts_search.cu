@@ -641,8 +641,8 @@ struct __align__(16) WarpSmem {
     float4 ghdr;           // their request's d_dn, d2u, q_first (and the request)
     uint4 dnext;           // the next tile's descriptor (asynchronous copy during the sweep)
     RecF cbox[32];         // bounding records of the tile's chunks (arrays that have them)
-    // exact-test queue, a first-in first-out ring carried from tile to tile: query index in the
-    // batch, entry position in its sorted array, tile | sel << 29, query index within its request
+    // exact-test queue, first in first out, carried from tile to tile: query index in the batch,
+    // entry position in its sorted array, tile | sel << 29, query index within its request
     uint32_t q_qi[PK_QUEUE], q_pos[PK_QUEUE], q_tile[PK_QUEUE], q_ql[PK_QUEUE];
     uint32_t plist[PK_PLIST];  // (member << 8 | slot) pairs of a chunk that passed the box test
     unsigned long long bar[PK_STAGES];
@@ -654,7 +654,6 @@ struct __align__(16) WarpSmem {
 };
 
 enum { PASS_COUNT = 0, PASS_WRITE = 1 };
-static_assert((PK_QUEUE & (PK_QUEUE - 1)) == 0 && PK_QUEUE >= 64, "the queue is a power-of-2 ring");
 
 // Flag in a tile descriptor's group word, set by the count pass on a tile with a hit that the
 // scratch did not keep: the write pass sweeps exactly the flagged tiles (k_place writes the rows
@@ -676,7 +675,6 @@ struct PairParams {
     // > 0 (tests only): the first warp of block 0 waits this long on a barrier phase that never
     // completes before taking any tile, so the kernel's timeout path runs (status, return)
     uint64_t stall_ns;
-    uint32_t fp64_warps;  // warps of a block that run exact tests at once (0: no limit)
 };
 
 // Exact FP64 test of one (query, entry) pair and, when `interval`, its hit interval. Not inlined:
@@ -712,12 +710,6 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
     const unsigned FULL = 0xffffffffu;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const PipeBufs &B = P.b;
-    // warps of the block running exact tests: a warp whose queue holds a full batch drains it
-    // only while fewer than P.fp64_warps others do (or when its queue has no room left), and
-    // sweeps on otherwise, so that the FP64 pipe is fed by a few warps while the others sweep
-    __shared__ unsigned fp64_busy;
-    if (threadIdx.x == 0) fp64_busy = 0u;
-    __syncthreads();
 
     if (lane == 0) {
         for (int k = 0; k < 4; k++) W.sweep[k] = 0;
@@ -749,21 +741,27 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         ntiles = 0;
     }
     unsigned long long acc_tests = 0, acc_exact = 0, acc_hits = 0;
-    uint32_t qn = 0, qh = 0;                    // queued candidates, ring head (warp-uniform)
+    uint32_t qn = 0;                            // queued candidates (warp-uniform)
     uint32_t wt_cur = 0xffffffffu, wt_cnt = 0;  // last tile with hits, its hits so far
 
     // Exact test of the oldest nflush queued candidates, one per lane.
     auto flush = [&](uint32_t nflush) {
         uint32_t qi = 0, pos = 0, tw = 0xffffffffu, ql = 0;
         if ((uint32_t)lane < nflush) {
-            const uint32_t j = (qh + lane) & (PK_QUEUE - 1);
-            qi = W.q_qi[j];
-            pos = W.q_pos[j];
-            tw = W.q_tile[j];
-            ql = W.q_ql[j];
+            qi = W.q_qi[lane];
+            pos = W.q_pos[lane];
+            tw = W.q_tile[lane];
+            ql = W.q_ql[lane];
         }
         __syncwarp();
-        qh = (qh + nflush) & (PK_QUEUE - 1);
+        if (qn > nflush && (uint32_t)lane < qn - nflush) {
+            const uint32_t j = nflush + lane;
+            W.q_qi[lane] = W.q_qi[j];
+            W.q_pos[lane] = W.q_pos[j];
+            W.q_tile[lane] = W.q_tile[j];
+            W.q_ql[lane] = W.q_ql[j];
+        }
+        __syncwarp();
         qn -= nflush;
         acc_exact += nflush;
         bool h = false;
@@ -824,48 +822,6 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         const uint32_t last_n = __popc(__shfl_sync(FULL, mine, last));
         wt_cnt = (last_tile == wt_cur ? wt_cnt : 0u) + last_n;
         wt_cur = last_tile;
-    };
-
-    // Exact tests of the queue's full batches, when the block's FP64 budget allows (or when the
-    // queue must make room for the next candidates: must_drain).
-    auto drain = [&](bool must_drain) {
-        bool got = P.fp64_warps == 0;
-        if (!got) {
-            unsigned ok = 0u;
-            if (lane == 0) {
-                if (atomicAdd(&fp64_busy, 1u) < P.fp64_warps) {
-                    ok = 1u;
-                } else {
-                    atomicSub(&fp64_busy, 1u);
-                    if (must_drain) {
-                        // wait (bounded) for a warp to finish its exact tests; after 50 ms the
-                        // batch runs anyway (the limit only shapes performance)
-                        const uint64_t t0 = globaltimer_ns();
-                        while (!ok) {
-                            __nanosleep(64);
-                            if (atomicAdd(&fp64_busy, 1u) < P.fp64_warps) {
-                                ok = 1u;
-                            } else {
-                                atomicSub(&fp64_busy, 1u);
-                                if (globaltimer_ns() - t0 > 50000000ull) break;
-                            }
-                        }
-                        if (!ok) {
-                            atomicAdd(&fp64_busy, 1u);  // run over the limit, released below
-                            ok = 1u;
-                        }
-                    }
-                }
-            }
-            got = __shfl_sync(FULL, ok, 0) != 0u;
-            if (!got) return;  // sweep on; the batches wait in the queue
-        }
-        while (qn >= 32) {
-            __syncwarp();
-            flush(32);
-        }
-        __syncwarp();
-        if (P.fp64_warps && lane == 0) atomicSub(&fp64_busy, 1u);
     };
 
     // tiles are taken from a device counter; the next index and its descriptor are fetched
@@ -956,7 +912,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
             const unsigned bm = __ballot_sync(FULL, p);
             if (bm) {
                 if (p) {
-                    const uint32_t j = (qh + qn + __popc(bm & lt_mask)) & (PK_QUEUE - 1);
+                    const uint32_t j = qn + __popc(bm & lt_mask);
                     W.q_qi[j] = qi;
                     W.q_pos[j] = pos;
                     W.q_tile[j] = tw;
@@ -965,7 +921,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 qn += __popc(bm);
                 if (qn >= 32) {
                     __syncwarp();
-                    drain(qn > PK_QUEUE - 32);
+                    flush(32);
                 }
             }
         };
@@ -1125,9 +1081,9 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         D = W.dnext;
         __syncwarp();  // (read by every lane before the next copy)
     }
-    while (!abort && qn) {
+    if (!abort && qn) {
         __syncwarp();
-        flush(qn < 32 ? qn : 32);
+        flush(qn);
     }
     if (abort) {
         if (lane == 0) atomicOr(B.status, DEV_ERR_TIMEOUT);
@@ -1234,7 +1190,6 @@ void fill_pair_params(PairParams &P, const Index *ix, const ReqDesc *reqs, const
     P.scap = c.scratch;
     P.tile = c.tile;
     P.stall_ns = 0;
-    P.fp64_warps = PK_FP64_WARPS;
 }
 
 // A stall requested for the next count pass (tests of the timeout path), taken by that launch.

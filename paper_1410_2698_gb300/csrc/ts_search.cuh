@@ -20,8 +20,7 @@ constexpr int PK_WARPS = 8;
 constexpr int PK_THREADS = PK_WARPS * 32;
 constexpr int PK_CH = 64;      // records per bulk-copy stage (2 KB): 2 per lane
 constexpr int PK_STAGES = 2;   // chunk stages per warp (copies in flight while one is swept)
-constexpr int PK_QUEUE = 256;  // exact-test queue per warp: a ring of up to 8 batches of 32
-constexpr int PK_FP64_WARPS = 2;  // warps of a block running exact tests at once (0: no limit)
+constexpr int PK_QUEUE = 64;   // exact-test queue per warp (drained at 32)
 constexpr uint32_t PK_PLIST = 128;  // box-test survivors of a chunk awaiting the gap bound
 constexpr uint32_t PK_MAX_TILES = (1u << 29) - 1;  // tile index bits of a queued candidate
 constexpr int PK_SPARSE = 8;  // chunks met by at most this many members: per-member sweep
