@@ -900,12 +900,18 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 acc_tests += bnd > a ? bnd - a : 0u;
             }
         }
-        // the axis of the stage-1 sweep, the one on which the array's entries are least likely
-        // to meet the query: time for grid cells (a cell holds entries of every time), y for an
-        // X subbin (its entries overlap the query in x by construction), x otherwise
-        const int dim = sel == SEL_GRID ? 3 : (sel == SEL_X ? 1 : 0);
-        const float fa = dim == 3 ? ea.w : (dim == 1 ? ea.y : ea.x);
-        const float fb = dim == 3 ? eb.w : (dim == 1 ? eb.y : eb.x);
+        // the two axes of the stage-1 sweep, those on which the array's entries are least likely
+        // to meet the query: time and x for grid cells (a cell holds entries of every time), the
+        // two other axes for a subbin array (its entries overlap the query in the subbin's axis
+        // by construction), y and z for the x-ordered temporal bins (a chunk's entries are close
+        // in x, and the chunk's bounding record has been tested already)
+        const int dim = sel == SEL_GRID ? 3 : (sel == SEL_X || sel == SEL_T ? 1 : 0);
+        const int dim2 = sel == SEL_GRID ? 0 : (sel == SEL_Z ? 1 : 2);
+        auto comp = [](const float4 &v, int k) {
+            return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+        };
+        const float fa = comp(ea, dim), fb = comp(eb, dim);
+        const float ga = comp(ea, dim2), gb = comp(eb, dim2);
 
         // a candidate that passed the filters joins the exact-test queue
         auto enqueue = [&](bool p, uint32_t qi, uint32_t pos) {
@@ -1026,17 +1032,19 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 }
                 if (npl) drain();
             } else {
-                // stage 1: one axis of every slot against every member (slot i is read at a
-                // warp-uniform address, a shared-memory broadcast); bit i is set when the axis
-                // extents overlap. Four independent accumulators per half keep the OR chains
+                // stage 1: two axes of every slot against every member (slot i is read at a
+                // warp-uniform address, a shared-memory broadcast); bit i is set when the extents
+                // overlap on both. Four independent accumulators per half keep the OR chains
                 // short.
                 if (PASS == PASS_COUNT && lane == 0) W.sweep[1]++;
                 const float2 *ax = reinterpret_cast<const float2 *>(&W.stage[st][0]) + dim;
+                const float2 *ax2 = reinterpret_cast<const float2 *>(&W.stage[st][0]) + dim2;
                 uint32_t a[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
                 for (int i = 0; i < 64; i++) {
-                    const float2 v = ax[4 * i];
-                    if ((v.y >= fa) & (v.x <= fb)) a[(i >> 5) * 4 + (i & 3)] |= 1u << (i & 31);
+                    const float2 v = ax[4 * i], u = ax2[4 * i];
+                    if ((v.y >= fa) & (v.x <= fb) & (u.y >= ga) & (u.x <= gb))
+                        a[(i >> 5) * 4 + (i & 3)] |= 1u << (i & 31);
                 }
                 m0 = ((a[0] | a[1]) | (a[2] | a[3])) & v0;
                 m1 = ((a[4] | a[5]) | (a[6] | a[7])) & v1;
