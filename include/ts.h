@@ -101,7 +101,7 @@ typedef struct ts_search_stats {
     double ms_write_pass; /* device time of the pair kernel's write pass (CUDA events) */
     /* how the pair kernel's count pass swept the candidates (diagnostics): */
     uint64_t n_chunks;    /* (tile, chunk of 64 entries) pairs swept */
-    uint64_t n_dense;     /* chunks swept by the one-axis bitmask (more than 8 members meet them) */
+    uint64_t n_dense;     /* chunks swept by the two-axis bitmask (more than 8 members meet them) */
     uint64_t n_sparse;    /* (member, chunk) visits of the per-member path (few members meet) */
     uint64_t n_stage2;    /* bitmask survivors given the full FP32 box and gap filters */
 } ts_search_stats;

@@ -68,7 +68,7 @@ enum : uint32_t {
 enum : int {
     ST_QSEGS = 0, ST_TESTS = 1, ST_EXACT = 2, ST_HITS = 3, ST_TILES = 4, ST_GROUPS = 5,
     ST_SUBBIN = 6, ST_SCRATCH = 7,  // ST_SCRATCH: hits offered to the scratch
-    // pair kernel sweep (count pass): chunks swept, chunks swept by the one-axis bitmask, member
+    // pair kernel sweep (count pass): chunks swept, chunks swept by the two-axis bitmask, member
     // visits of the sparse path, survivors of the bitmask given the full FP32 filters
     ST_CHUNKS = 8, ST_DENSE = 9, ST_SPARSE = 10, ST_STAGE2 = 11, ST_NSLOTS = 12
 };
