@@ -670,6 +670,9 @@ def _index_params(index):
     return {}
 
 
+E2E_CHUNK_ROWS = 1 << 27  # rows per read of the end-to-end step (3 GB of pinned host memory)
+
+
 def _pinned_rows(n):
     """Pinned host buffers for n result rows (numpy views of page-locked torch tensors)."""
     import torch
@@ -683,16 +686,25 @@ def _pinned_rows(n):
 
 def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
     """The batched step through the C ABI with HOST buffers: the query columns live in pinned
-    host memory (the plans read them from there) and every result row is copied into pinned host
-    buffers inside the timed region (wall clock, the stream synchronised on both sides). With
-    make_plan (plans that do not fit together) each index's plan is created, timed over the steps
-    and released in turn."""
+    host memory (the plans read them from there) and every result row is read back into pinned
+    host memory inside the timed region (wall clock, the stream synchronised on both sides), in
+    chunks of at most E2E_CHUNK_ROWS rows through one pinned buffer (the host memory it holds stays
+    bounded whatever the step's rows, also with one process per GPU). With make_plan (plans that
+    do not fit together) each index's plan is created, timed over the steps and released in
+    turn."""
     import torch
     from paper_1410_2698_gb300.workloads import Segments
     qhost = {f: torch.from_numpy(np.ascontiguousarray(getattr(w.queries, f))).pin_memory()
              for f in Segments.FIELDS}
     reqs = api.prepare_requests([(qhost, d, w.t_start, w.t_end) for d in w.distances])
-    rows_out, keep = _pinned_rows(max_rows)
+    rows_out, keep = _pinned_rows(min(max_rows, E2E_CHUNK_ROWS))
+
+    def read_rows(plan, total):
+        """Every row of the plan's last run, chunk by chunk; returns the bytes read."""
+        n = 0
+        for first in range(0, total, E2E_CHUNK_ROWS):
+            n += plan.copy_rows(first, min(E2E_CHUNK_ROWS, total - first), rows_out)
+        return n
     if make_plan is not None:
         total_ms, copy_ms, h2d, d2h, qsegs = 0.0, 0.0, 0, 0, 0
         copies = []
@@ -707,8 +719,7 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
                 plan.run(reqs)
                 st = plan.wait()
                 t1 = time.perf_counter()
-                rows, _ = plan.rows_to_host(out=rows_out)  # every request's rows, one copy
-                d2h += sum(v.nbytes for v in rows.values())
+                d2h += read_rows(plan, st["rows"])  # every request's rows
                 torch.cuda.synchronize()
                 t2 = time.perf_counter()
                 total_ms += (t2 - t0) * 1e3
@@ -738,10 +749,9 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
             st = plans[k].wait()
             q_s += st["stats"]["n_qsegs"]
             c0 = time.perf_counter()
-            rows, _ = plans[k].rows_to_host(out=rows_out)  # every request's rows, one copy
+            d2h_s += read_rows(plans[k], st["rows"])  # every request's rows
             if s > 0:
                 copy_ms += (time.perf_counter() - c0) * 1e3
-            d2h_s += sum(v.nbytes for v in rows.values())
             h2d_s += 8 * 8 * w.queries.n * reqs.n
         torch.cuda.synchronize()
         if s > 0:  # the first pass is warm-up

@@ -466,6 +466,17 @@ class BatchPlan:
             out = {k: v[order] for k, v in out.items()}
         return out
 
+    def copy_rows(self, first, count, out):
+        """Copy rows [first, first + count) of the last run into the first `count` entries of
+        `out` (a dict of q_idx, e_idx, t_in, t_out host arrays, e.g. views of pinned buffers)."""
+        if any(len(out[k]) < count for k in ("q_idx", "e_idx", "t_in", "t_out")):
+            raise ValueError(f"output buffers hold fewer than {count} rows")
+        if count:
+            check(_lib.load().ts_batch_copy_rows(
+                self._h, int(first), int(count), out["q_idx"].ctypes.data,
+                out["e_idx"].ctypes.data, out["t_in"].ctypes.data, out["t_out"].ctypes.data))
+        return 24 * int(count)
+
     def rows_to_host(self, out=None):
         """Copy every row of the last run (requests in order, each request's rows contiguous) to
         host arrays in one call: new numpy arrays or the first rows of `out`. Returns the rows
