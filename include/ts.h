@@ -327,7 +327,7 @@ ts_status ts_server_wait(ts_server *srv, uint64_t ticket, uint32_t timeout_ms, t
 
 /* The server's device-memory accounting: its budget (mem_budget_bytes, or the one derived at
  * creation), the bytes its batch plans hold, and the bytes of result rows not yet released (any
- * pointer may be NULL). */
+ * pointer may be NULL). A service of the request loop; the paper has no counterpart. */
 ts_status ts_server_info(ts_server *srv, uint64_t *budget_bytes, uint64_t *plan_bytes,
                          uint64_t *held_bytes);
 
