@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--served-max-traj", type=int, default=0,
                     help="largest request, in query trajectories (0 = 5,000 on the merger-like "
                          "database, 500 otherwise)")
+    ap.add_argument("--served-inflight", type=int, default=2,
+                    help="batches of the served loop on the device at once")
     ap.add_argument("--served-rho", default="0.5,0.9,1.5",
                     help="Poisson arrival rates as multiples of the plain request rate")
     ap.add_argument("--served-only", action="store_true",
@@ -830,8 +832,9 @@ def run_served(args, api, w, index, tile=0):
         th.join()
         return time.perf_counter() - start, lat
     srv = api.Server(index, max_batch_requests=64, max_batch_queries=max(1 << 20, 2 * max_q),
-                     max_batch_rows=max(1 << 25, 2 * max_rows), max_inflight=2, use_graph=True,
-                     linger_us=200, tile_records=tile)
+                     max_batch_rows=max(1 << 25, 2 * max_rows),
+                     max_inflight=args.served_inflight, use_graph=True, linger_us=200,
+                     tile_records=tile)
     rhos = [float(x) for x in str(args.served_rho).split(",") if x]
     try:
         def serve(arrivals):
@@ -883,7 +886,7 @@ def run_served(args, api, w, index, tile=0):
     if rows_plain != rows_sat:
         raise RuntimeError("served and plain forms disagree on the result count")
     return {
-        "index": index_kind_name(index),
+        "index": index_kind_name(index), "max_inflight": args.served_inflight,
         "requests": len(stream), "query_segs": qsegs, "rows": rows_plain,
         "workload": f"{len(stream)} requests on the resident {w.name} database: 1-{max_traj} "
                     f"query trajectory runs (log-uniform) of 10-200 segments, interval = the "
