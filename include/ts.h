@@ -290,7 +290,11 @@ typedef struct ts_server_params {
     uint32_t tile_records;        /* as in ts_batch_params */
     int32_t use_graph;            /* replay each batch plan as a CUDA graph */
     uint32_t linger_us;           /* how long a partly filled batch waits for more requests */
-    uint32_t reserved;            /* 0 */
+    uint32_t admit_wait_ms;       /* how long a counted batch waits for room in the memory budget
+                                     before it is admitted beyond the budget, if the device has
+                                     the memory (0 = 1000 ms); results that completed but were
+                                     not yet collected hold budget too, so an unbounded wait
+                                     could wait on a client that waits on this batch */
     uint64_t scratch_rows;        /* hits a batch's count pass keeps for placement (0 = derived
                                      from the budget: an eighth of it per plan, at 32 B per
                                      hit); the tiles of hits beyond it are swept a second time */
@@ -298,8 +302,9 @@ typedef struct ts_server_params {
                                      and scratch) and the rows of results not yet released
                                      (0 = three quarters of the free device memory at creation).
                                      A batch whose rows do not fit beside the rows still held
-                                     waits (its plan idle) until results are released; one whose
-                                     rows alone exceed the budget is split */
+                                     waits (its plan idle) until results are released, for at
+                                     most admit_wait_ms; one whose rows alone exceed the budget
+                                     is split */
 } ts_server_params;
 
 typedef struct ts_server ts_server;

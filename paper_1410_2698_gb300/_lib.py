@@ -93,7 +93,7 @@ class ts_server_params(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_uint32), ("max_batch_requests", ctypes.c_uint32),
                 ("max_batch_queries", ctypes.c_uint64), ("max_batch_rows", ctypes.c_uint64),
                 ("tile_records", ctypes.c_uint32), ("use_graph", ctypes.c_int32),
-                ("linger_us", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("linger_us", ctypes.c_uint32), ("admit_wait_ms", ctypes.c_uint32),
                 ("scratch_rows", ctypes.c_uint64), ("mem_budget_bytes", ctypes.c_uint64)]
 
 

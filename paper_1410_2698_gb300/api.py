@@ -518,12 +518,12 @@ class Server:
 
     def __init__(self, index: Index, max_batch_requests=64, max_batch_queries=1 << 20,
                  max_batch_rows=1 << 26, max_inflight=2, tile_records=0, use_graph=True,
-                 linger_us=200, scratch_rows=0, mem_budget_bytes=0):
+                 linger_us=200, scratch_rows=0, mem_budget_bytes=0, admit_wait_ms=0):
         lib = _lib.load()
         p = _lib.ts_server_params(int(max_inflight), int(max_batch_requests),
                                   int(max_batch_queries), int(max_batch_rows),
-                                  int(tile_records), int(use_graph), int(linger_us), 0,
-                                  int(scratch_rows), int(mem_budget_bytes))
+                                  int(tile_records), int(use_graph), int(linger_us),
+                                  int(admit_wait_ms), int(scratch_rows), int(mem_budget_bytes))
         h = ctypes.c_void_p()
         check(lib.ts_server_create(index.handle, ctypes.byref(p), ctypes.byref(h)))
         self._h = h

@@ -60,6 +60,7 @@ struct Slot {
     bool busy = false;
     int phase = SLOT_IDLE;
     uint64_t rows = 0;  // the batch's rows (count phase done)
+    double admit_since_us = 0;  // when the batch started waiting for room in the budget
     std::shared_ptr<RowBlock> block;
 };
 
@@ -76,7 +77,7 @@ struct Server {
     std::deque<SrvReq *> queue;
     std::unordered_map<uint64_t, SrvReq *> reqs;
     std::thread th;
-    bool stop = false;
+    std::atomic<bool> stop{false};  // set under mu; read also by the loop outside it
     uint64_t next_ticket = 1;
     size_t split_limit = 0;  // after an overflow: at most this many requests in the next batch
     // device-memory budget: the plans' own bytes, and the bytes of live row blocks (updated by
@@ -185,6 +186,7 @@ void count_done(Server *s, Slot &sl)
     if (st == TS_OK && bs.rows > 0) {
         sl.rows = bs.rows;
         sl.phase = SLOT_ADMIT;
+        sl.admit_since_us = s->now_us();
         try_admit(s, sl);
         return;
     }
@@ -210,18 +212,29 @@ void end_batch(Server *s, Slot &sl, ts_status st)
 
 // Admission of a counted batch's rows: when they fit in the budget beside the rows still held
 // (or nothing else is held), allocate them and launch the write phase; otherwise the slot stays
-// in SLOT_ADMIT and the loop tries again. An allocation that fails while other rows are held is
-// retried the same way.
+// in SLOT_ADMIT and the loop tries again. The budget is soft: after admit_wait_ms the batch is
+// admitted beyond it if the device has the memory (the rows held may belong to results that
+// completed but that the client has not collected yet, perhaps because it waits on this batch).
+// An allocation that fails while other rows are held is retried until ten times that wait (at
+// least 10 s), then the batch ends with TS_ERR_OOM; a stopping server cancels waiting batches.
 void try_admit(Server *s, Slot &sl)
 {
+    if (s->stop) {
+        set_error("server stopped before the batch's rows were admitted");
+        end_batch(s, sl, TS_ERR_CANCELLED);
+        return;
+    }
     const uint64_t need = ROW_BYTES * sl.rows;
     const int64_t held = s->held->load();
-    if (held > 0 && (uint64_t)held + need > s->row_budget()) return;  // wait for releases
+    const double wait_ms = s->prm.admit_wait_ms ? (double)s->prm.admit_wait_ms : 1000.0;
+    const double waited_ms = (s->now_us() - sl.admit_since_us) / 1e3;
+    if (held > 0 && (uint64_t)held + need > s->row_budget() && waited_ms < wait_ms)
+        return;  // wait for releases
     BatchPlan *p = sl.plan;
     auto block = std::make_shared<RowBlock>();
     block->held = s->held;
     ts_status st = block->alloc(sl.rows, p->stream);
-    if (st == TS_ERR_OOM && held > 0) {
+    if (st == TS_ERR_OOM && held > 0 && waited_ms < std::max(10.0 * wait_ms, 10000.0)) {
         cudaGetLastError();
         return;  // retry after results are released
     }

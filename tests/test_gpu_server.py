@@ -134,7 +134,7 @@ def test_server_defers_a_batch_until_results_release_memory():
     reqs = [(w.queries, 25.0, 0.0, 70.0), (w.queries.take(np.arange(1500)), 20.0, 0.0, 70.0)]
     rows = [api.ts_search(idx, q, d, ts, te).count for q, d, ts, te in reqs]
     kw = dict(max_batch_requests=1, max_batch_queries=4000, max_batch_rows=1 << 26,
-              max_inflight=1, linger_us=0, scratch_rows=1 << 16)
+              max_inflight=1, linger_us=0, scratch_rows=1 << 16, admit_wait_ms=60000)
     probe = api.Server(idx, mem_budget_bytes=1 << 40, **kw)
     plan_bytes = probe.info()["plan_bytes"]
     probe.close()
@@ -158,4 +158,40 @@ def test_server_defers_a_batch_until_results_release_memory():
     assert tm1["done_us"] - tm1["submit_us"] >= 1.0e6  # it waited for the release
     res1.free()
     assert srv.info()["held_bytes"] == 0
+    srv.close()
+
+
+def test_server_admits_beyond_the_budget_after_the_admission_wait():
+    """The budget is soft: a client that holds one result and waits on the next must not wait
+    forever. With a budget that fits one request's rows and a 200 ms admission wait, the second
+    request completes -- equal to the oracle -- while the first result is still held, and
+    destroying a server whose batch waits for memory cancels that batch instead of hanging."""
+    w = workloads.tiny()
+    idx = api.ts_build_index(w.db, kind="temporal")
+    reqs = [(w.queries, 25.0, 0.0, 70.0), (w.queries.take(np.arange(1500)), 20.0, 0.0, 70.0)]
+    rows = [api.ts_search(idx, q, d, ts, te).count for q, d, ts, te in reqs]
+    kw = dict(max_batch_requests=1, max_batch_queries=4000, max_batch_rows=1 << 26,
+              max_inflight=1, linger_us=0, scratch_rows=1 << 16)
+    probe = api.Server(idx, mem_budget_bytes=1 << 40, **kw)
+    plan_bytes = probe.info()["plan_bytes"]
+    probe.close()
+    budget = plan_bytes + 24 * max(rows) + 24 * min(rows) // 2
+    srv = api.Server(idx, mem_budget_bytes=budget, admit_wait_ms=200, **kw)
+    res0, _ = srv.wait(srv.submit(*reqs[0]), timeout_ms=60000)
+    t1 = srv.submit(*reqs[1])
+    res1, tm1 = srv.wait(t1, timeout_ms=60000)  # res0 still held
+    assert tm1["done_us"] - tm1["submit_us"] >= 0.2e6
+    assert srv.info()["held_bytes"] == 24 * (rows[0] + rows[1])
+    q, d, ts, te = reqs[1]
+    parity.compare(res1.to_host(sort=True), oracle.search(w.db, q, ts, te, d), w.db, q, ts,
+                   te, d)
+    res1.free()
+    # a batch left waiting for memory when the server is destroyed is cancelled
+    srv2 = api.Server(idx, mem_budget_bytes=budget, admit_wait_ms=60000, **kw)
+    srv2.submit(*reqs[1])
+    time.sleep(0.5)
+    t0 = time.perf_counter()
+    srv2.close()
+    assert time.perf_counter() - t0 < 10.0
+    res0.free()
     srv.close()
