@@ -143,17 +143,6 @@ static __device__ __forceinline__ bool mag_lt(double x, double y)
     return (dbits(x) & 0x7fffffffffffffffll) < (dbits(y) & 0x7fffffffffffffffll);
 }
 
-// Division-free hit decision: the minimum of a tau^2 + 2 b tau + c over [0, T] is <= 0 (a >= 0,
-// T > 0). The branch tests are sign and magnitude tests on the integer pipe: a is a sum of
-// squares, and -b and aT are compared only when b < 0.
-static __device__ __forceinline__ bool quad_hit(const Quad &k)
-{
-    if (zero(k.a) || !neg(k.b)) return nonpos(k.c);           // minimum at tau = 0
-    const double aT = k.a * k.T;
-    if (!mag_lt(k.b, aT)) return nonpos(fma(aT + 2.0 * k.b, k.T, k.c));  // at tau = T (-b >= aT)
-    return !neg(fma(k.b, k.b, -(k.a * k.c)));                  // interior minimum
-}
-
 // |x| within [2^-1000, 2^1000) (its biased exponent, sign ignored): the range where the refined
 // estimates below are accurate (no subnormal estimate, no overflow of x * y).
 static __device__ __forceinline__ bool nr_range(double x)
@@ -163,48 +152,66 @@ static __device__ __forceinline__ bool nr_range(double x)
 }
 
 // 1/x by Newton-Raphson from the hardware estimate (rcp.approx.ftz.f64, about 20 good bits): one
-// third-order step y + y e + y e^2 with e = 1 - x y cubes the estimate's relative error, leaving
-// only the rounding of the last steps (a few ulps). For x in the nr_range.
+// second-order step y + y e with e = 1 - x y squares the estimate's relative error, to about
+// 2^-40 (measured 2^-39.9 over the range): a thousandth of the 1e-9 interval tolerance, for two
+// FP64 instructions. For x in the nr_range.
 static __device__ __forceinline__ double rcp_nr(double x)
 {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
     const double e = fma(-x, y, 1.0);
-    return fma(y, fma(e, e, e), y);
+    return fma(y, e, y);
 }
 
-// sqrt(x) by Newton-Raphson from the hardware estimate of 1/sqrt(x) (rsqrt.approx.ftz.f64): the
-// coupled iteration on g ~ sqrt(x), h ~ 1/(2 sqrt(x)) (r = 1/2 - g h; g += g r; h += h r), then
-// one Newton correction of g with the residual x - g^2. For x in the nr_range (the estimate is
-// then a normal number, and halving it is a decrement of its exponent, on the integer pipe).
+// sqrt(x) by Newton-Raphson from the hardware estimate y of 1/sqrt(x) (rsqrt.approx.ftz.f64):
+// g = x y ~ sqrt(x), then one Newton correction of g with the residual x - g^2 and h = y / 2 ~
+// 1/(2 sqrt(x)). With y of relative error eps, the result's is about 1.5 eps^2 (measured 2^-39.5
+// over the range). For x in the nr_range (the estimate is then a normal number, and halving it is
+// a decrement of its exponent, on the integer pipe).
 static __device__ __forceinline__ double sqrt_nr(double x)
 {
     double y;
     asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
     double g = x * y, h = __longlong_as_double(dbits(y) - (1ll << 52));
-    const double r = fma(-g, h, 0.5);
-    g = fma(g, r, g);
-    h = fma(h, r, h);
     return fma(fma(-g, g, x), h, g);
 }
 
-// Interval of a hit from the numerically stable root pair s/a, c/s (s = -(b + sign(b) sqrt(disc)),
-// disc = b^2 - a c). The square root and the two quotients come from the refined estimates
-// above (relative error of a few ulps, far inside the 1e-9 interval tolerance); values outside
-// their range take the library's sqrt and division.
+// Hit decision and, when `interval`, the hit interval [*tin, *tout].
 //
-// The roots need no comparison of their values: with s of the sign opposite to b's sign bit,
-// s/a is the smaller root when b's sign bit is clear and the larger when it is set (c/s is the
-// other), and every clamp below compares a value with 0 or two non-negative values, which the
-// integer pipe does on the bit patterns.
-static __device__ __forceinline__ void quad_interval(const Quad &k, double *tin, double *tout)
+// The decision is division-free: the minimum of a tau^2 + 2 b tau + c over [0, T] is <= 0 (a >= 0,
+// T > 0). Its branch tests are sign and magnitude tests on the integer pipe: a is a sum of
+// squares, and -b and aT are compared only when b < 0. The discriminant disc = b^2 - a c decides
+// an interior minimum and gives the roots, so it is computed once, before the branches (a warp
+// whose lanes take different branches issues every branch's instructions, so a value two
+// branches need is cheapest computed once for all lanes).
+//
+// The interval comes from the numerically stable root pair s/a, c/s (s = -(b + sign(b)
+// sqrt(disc))). The square root and the two quotients come from the refined estimates above
+// (relative error about 2^-40 each, so a few 1e-12 of the roots: far inside the 1e-9 interval
+// tolerance); values outside their range take the library's sqrt and division. The roots need no comparison of their values: with
+// s of the sign opposite to b's sign bit, s/a is the smaller root when b's sign bit is clear and
+// the larger when it is set (c/s is the other), and every clamp compares a value with 0 or two
+// non-negative values, which the integer pipe does on the bit patterns.
+static __device__ __forceinline__ bool quad_solve(const Quad &k, bool interval, double *tin,
+                                                  double *tout)
 {
+    double disc = fma(k.b, k.b, -(k.a * k.c));
+    bool hit;
+    if (zero(k.a) || !neg(k.b)) {
+        hit = nonpos(k.c);                                         // minimum at tau = 0
+    } else {
+        const double aT = k.a * k.T;
+        if (!mag_lt(k.b, aT))
+            hit = nonpos(fma(fma(2.0, k.b, aT), k.T, k.c));        // at tau = T (-b >= aT)
+        else
+            hit = !neg(disc);                                      // interior minimum
+    }
+    if (!hit || !interval) return hit;
     double lower, upper;
     if (zero(k.a)) {
         lower = 0.0;
         upper = k.T;
     } else {
-        double disc = fma(k.b, k.b, -(k.a * k.c));
         if (neg(disc)) disc = 0.0;  // only reachable within rounding of a tangency
         const double sq = nr_range(disc) ? sqrt_nr(disc) : sqrt(disc);
         const double s = -(k.b + copysign(sq, k.b));
@@ -224,6 +231,7 @@ static __device__ __forceinline__ void quad_interval(const Quad &k, double *tin,
     }
     *tin = k.t_lo + lower;
     *tout = k.t_lo + upper;
+    return true;
 }
 
 // Conservative FP32 filter, stage 1: the time extents overlap and the entry MBB meets the query

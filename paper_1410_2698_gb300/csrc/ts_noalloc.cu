@@ -147,10 +147,7 @@ __global__ void __launch_bounds__(NA_WARPS * 32) k_na_tiles(NaParams P)
                 double tin = 0.0, tout = 0.0;
                 if (p) {
                     Quad qd;
-                    if (pair_quad(M.q, e, M.q.pad, qd) && quad_hit(qd)) {
-                        h = true;
-                        if (PASS == 1) quad_interval(qd, &tin, &tout);
-                    }
+                    h = pair_quad(M.q, e, M.q.pad, qd) && quad_solve(qd, PASS == 1, &tin, &tout);
                 }
                 const unsigned hm = __ballot_sync(FULL, h);
                 if (PASS == 1 && h) {

@@ -686,9 +686,7 @@ __device__ __noinline__ bool exact_test(const QueryD *qp, const SegD *ep, bool i
     const SegD e = *ep;
     const QueryD q = *qp;
     Quad qd;
-    if (!(pair_quad(q, e, q.pad, qd) && quad_hit(qd))) return false;
-    if (interval) quad_interval(qd, tin, tout);
-    return true;
+    return pair_quad(q, e, q.pad, qd) && quad_solve(qd, interval, tin, tout);
 }
 
 // Persistent pair kernel. Warps take tiles (a group of up to 32 query units and up to `tile`
