@@ -95,31 +95,42 @@ struct Quad {
 // r0 = p_q(t_lo) - p_l(t_lo), dv = v_q - v_l, a = dv.dv, b = r0.dv, c = r0.r0 - d^2.
 // When the four window bounds have their sign bits clear (non-negative times, the usual case) the
 // window is found on the integer pipe: non-negative doubles order as their bit patterns.
-static __device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e, double dd, Quad &o)
+//
+// t_lo is the later of the two starts (the query's clipped w0, where its record holds its
+// position, or the entry's t0), so one of the two positions at t_lo is a start point as stored
+// and only the other segment is advanced, by dt = t_lo - its own start: s r0 = (p_adv + v_adv dt)
+// - p_start, where s = +1 when the query is the segment advanced and -1 when the entry is. The
+// sign reaches only b, and is put back with an exclusive-or of b's sign bit (integer pipe).
+static __device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e, Quad &o)
 {
     double t_lo, t_hi;
+    bool adv_q;  // the entry starts at t_lo (or both do): advance the query
     const long long a0 = __double_as_longlong(q.w0), b0 = __double_as_longlong(e.t0);
     const long long a1 = __double_as_longlong(q.w1), b1 = __double_as_longlong(e.t1);
     if ((a0 | b0 | a1 | b1) >= 0) {
-        const long long lo = a0 > b0 ? a0 : b0, hi = a1 < b1 ? a1 : b1;
+        adv_q = b0 >= a0;
+        const long long lo = adv_q ? b0 : a0, hi = a1 < b1 ? a1 : b1;
         if (!(lo < hi)) return false;
         t_lo = __longlong_as_double(lo);
         t_hi = __longlong_as_double(hi);
     } else {
-        t_lo = dmx(q.w0, e.t0);
+        adv_q = e.t0 >= q.w0;
+        t_lo = adv_q ? e.t0 : q.w0;
         t_hi = dmn(q.w1, e.t1);
         if (!(t_lo < t_hi)) return false;
     }
-    const double dq = t_lo - q.t0, de = t_lo - e.t0;
-    const double rx = fma(q.vx, dq, q.x0) - fma(e.vx, de, e.x0);
-    const double ry = fma(q.vy, dq, q.y0) - fma(e.vy, de, e.y0);
-    const double rz = fma(q.vz, dq, q.z0) - fma(e.vz, de, e.z0);
+    const double dt = t_lo - (adv_q ? q.w0 : e.t0);
+    const double rx = fma(adv_q ? q.vx : e.vx, dt, adv_q ? q.xw : e.x0) - (adv_q ? e.x0 : q.xw);
+    const double ry = fma(adv_q ? q.vy : e.vy, dt, adv_q ? q.yw : e.y0) - (adv_q ? e.y0 : q.yw);
+    const double rz = fma(adv_q ? q.vz : e.vz, dt, adv_q ? q.zw : e.z0) - (adv_q ? e.z0 : q.zw);
     const double dvx = q.vx - e.vx, dvy = q.vy - e.vy, dvz = q.vz - e.vz;
     o.t_lo = t_lo;
     o.T = t_hi - t_lo;
     o.a = fma(dvz, dvz, fma(dvy, dvy, dvx * dvx));
-    o.b = fma(rz, dvz, fma(ry, dvy, rx * dvx));
-    o.c = fma(rz, rz, fma(ry, ry, fma(rx, rx, -dd)));
+    const double sb = fma(rz, dvz, fma(ry, dvy, rx * dvx));  // s b
+    o.b = __longlong_as_double(__double_as_longlong(sb) ^
+                               (adv_q ? 0ll : (long long)0x8000000000000000ull));
+    o.c = fma(rz, rz, fma(ry, ry, fma(rx, rx, -q.dd)));
     return true;
 }
 

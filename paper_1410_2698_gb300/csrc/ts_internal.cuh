@@ -37,11 +37,12 @@ struct __align__(16) SegD {
 };
 static_assert(sizeof(SegD) == 64, "SegD is 64 bytes");
 
-// Exact data of one query segment: start point and time, velocity, clipped window [w0, w1].
+// Exact data of one query segment: its position at the start w0 of its clipped window [w0, w1],
+// its velocity, and the request's d^2.
 struct __align__(16) QueryD {
-    double x0, y0, z0, t0;
-    double vx, vy, vz, w0;
-    double w1, pad;
+    double xw, yw, zw, w0;
+    double vx, vy, vz, w1;
+    double dd, pad;
 };
 static_assert(sizeof(QueryD) == 80, "QueryD is 80 bytes");
 

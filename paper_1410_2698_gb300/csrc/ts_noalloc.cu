@@ -91,13 +91,17 @@ __global__ void __launch_bounds__(NA_WARPS * 32) k_na_tiles(NaParams P)
             if (!fin || !(v[7] > v[3])) atomicOr(&ctrl->status, DEV_ERR_INVALID);
             const double dt = v[7] - v[3];
             NaMember &M = mem[wid][lane];
-            M.q.x0 = v[0]; M.q.y0 = v[1]; M.q.z0 = v[2]; M.q.t0 = v[3];
             M.q.vx = (v[4] - v[0]) / dt;
             M.q.vy = (v[5] - v[1]) / dt;
             M.q.vz = (v[6] - v[2]) / dt;
             M.q.w0 = dmx(v[3], P.Ts);
             M.q.w1 = dmn(v[7], P.Te);
-            M.q.pad = P.dd;
+            const double dw = M.q.w0 - v[3];  // 0 unless the request interval clips the start
+            M.q.xw = fma(M.q.vx, dw, v[0]);
+            M.q.yw = fma(M.q.vy, dw, v[1]);
+            M.q.zw = fma(M.q.vz, dw, v[2]);
+            M.q.dd = P.dd;
+            M.q.pad = 0.0;
             float mn[3], mx[3];
             for (int d = 0; d < 3; d++) {
                 mn[d] = __double2float_rd(v[d] < v[4 + d] ? v[d] : v[4 + d]);
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(NA_WARPS * 32) k_na_tiles(NaParams P)
                 double tin = 0.0, tout = 0.0;
                 if (p) {
                     Quad qd;
-                    h = pair_quad(M.q, e, M.q.pad, qd) && quad_solve(qd, PASS == 1, &tin, &tout);
+                    h = pair_quad(M.q, e, qd) && quad_solve(qd, PASS == 1, &tin, &tout);
                 }
                 const unsigned hm = __ballot_sync(FULL, h);
                 if (PASS == 1 && h) {

@@ -217,13 +217,17 @@ __global__ void k_qprep(PrepParams P)
         if (!fin || !(v[7] > v[3])) atomicOr(P.b.status, DEV_ERR_INVALID);
         const double dt = v[7] - v[3];
         QueryD q;
-        q.x0 = v[0]; q.y0 = v[1]; q.z0 = v[2]; q.t0 = v[3];
         q.vx = (v[4] - v[0]) / dt;
         q.vy = (v[5] - v[1]) / dt;
         q.vz = (v[6] - v[2]) / dt;
         q.w0 = dmx(v[3], R.t_start);
         q.w1 = dmn(v[7], R.t_end);
-        q.pad = R.dd;
+        const double dw = q.w0 - v[3];  // 0 unless the request interval clips the start
+        q.xw = fma(q.vx, dw, v[0]);
+        q.yw = fma(q.vy, dw, v[1]);
+        q.zw = fma(q.vz, dw, v[2]);
+        q.dd = R.dd;
+        q.pad = 0.0;
         const bool valid = fin && (v[7] > v[3]) && (q.w0 < q.w1);
         P.b.qd[i] = q;
         P.b.qreq[i] = r;
@@ -686,7 +690,7 @@ __device__ __noinline__ bool exact_test(const QueryD *qp, const SegD *ep, bool i
     const SegD e = *ep;
     const QueryD q = *qp;
     Quad qd;
-    return pair_quad(q, e, q.pad, qd) && quad_solve(qd, interval, tin, tout);
+    return pair_quad(q, e, qd) && quad_solve(qd, interval, tin, tout);
 }
 
 // Persistent pair kernel. Warps take tiles (a group of up to 32 query units and up to `tile`
