@@ -82,6 +82,32 @@ def test_well_conditioned_intervals_agree_with_the_oracle_to_rounding(tiny):
     assert e_in.max() <= 1e-11 and e_out.max() <= 1e-11, (e_in.max(), e_out.max())
 
 
+@pytest.mark.parametrize("kind", ["temporal", "spatiotemporal"])
+def test_query_clipped_by_the_request_start(tiny, kind):
+    """A request start T_s inside query segments: the query record then holds its position at
+    T_s (one rounding), and a pair whose entry starts later advances the query from there (a
+    second rounding, where the plain definition has one). The match set must equal the oracle's,
+    and on well-conditioned pairs of exactly that kind (query clipped at T_s, entry starting after
+    T_s) the interval ends must still agree with the oracle's to 1e-11 of the overlap."""
+    d, Ts, Te = 25.0, 37.3, 52.3  # ~23,000 hits, ~370 of them of the clipped kind
+    q = tiny.queries
+    ref = oracle.search(tiny.db, q, Ts, Te, d)
+    got, _, _ = _run(tiny.db, q, kind, d, Ts, Te)
+    parity.compare(got, ref, tiny.db, q, Ts, Te, d)
+    kg = (got["q_idx"].astype(np.int64) << 32) | got["e_idx"].astype(np.int64)
+    kr = (ref["q_idx"].astype(np.int64) << 32) | ref["e_idx"].astype(np.int64)
+    common, ig, ir = np.intersect1d(kg, kr, return_indices=True)
+    qi = ref["q_idx"][ir].astype(np.int64)
+    ei = ref["e_idx"][ir].astype(np.int64)
+    clipped = (q.t0[qi] < Ts) & (q.t1[qi] > Ts) & (tiny.db.t0[ei] > Ts)
+    well = clipped & (np.abs(ref["s_min"][ir] - d) > 1e-6 * d)
+    assert well.sum() > 200, well.sum()
+    T = parity.overlap_duration(tiny.db, q, qi, ei, Ts, Te)
+    e_in = np.abs(got["t_in"][ig] - ref["t_in"][ir])[well] / T[well]
+    e_out = np.abs(got["t_out"][ig] - ref["t_out"][ir])[well] / T[well]
+    assert e_in.max() <= 1e-11 and e_out.max() <= 1e-11, (e_in.max(), e_out.max())
+
+
 def test_deterministic_order(tiny):
     idx = api.ts_build_index(tiny.db, kind="spatiotemporal")
     a = api.ts_search(idx, tiny.queries, 5.0, 0, 70).to_host()
