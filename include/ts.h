@@ -394,7 +394,8 @@ ts_status ts_measure_alu_peaks(double *fp32_tflops, double *fp64_tflops);
 /* The exact test's reciprocal and square root beside the CUDA runtime's, for n values x (host
  * arrays of n doubles each; the call allocates a small device buffer and synchronises the device).
  * The interval of a hit (the roots s/a and c/s of Sec. 3.1's distance quadratic) uses a hardware
- * reciprocal or reciprocal-square-root estimate refined by Newton-Raphson steps; this call
+ * reciprocal or reciprocal-square-root estimate refined by one Newton-Raphson step (about 2^-40
+ * relative error, against the search's 1e-9 interval tolerance); this call
  * evaluates those refinements on the device (rcp_est, sqrt_est; NaN outside their range,
  * 2^-1000 <= |x| < 2^1000) and the correctly rounded 1/x and sqrt(x) (rcp_ref, sqrt_ref) so a
  * test can bound their difference. A diagnostic; the paper has no counterpart. */
