@@ -258,7 +258,8 @@ ts_status ts_batch_create(const ts_index *idx, const ts_batch_params *params, vo
 ts_status ts_batch_run(ts_batch *b, uint32_t nreq, const ts_segments *qs,
                        const ts_query_params *qps, void *stream);
 
-/* Wait for the last run and report its outcome. */
+/* Wait for the last run (only for it and the work enqueued before it on its stream: plans that
+ * share a stream, run one after another, are waited for one by one) and report its outcome. */
 ts_status ts_batch_wait(ts_batch *b, ts_batch_status *status);
 
 /* Rows of request r of the last run: [first, first + count) of the plan's row arrays, whose
@@ -268,8 +269,9 @@ ts_status ts_batch_request_rows(const ts_batch *b, uint32_t r, uint64_t *first, 
 ts_status ts_batch_rows(const ts_batch *b, const uint32_t **q_idx, const uint32_t **e_idx,
                         const double **t_in, const double **t_out);
 
-/* Copy rows [first, first + count) of the last run to host arrays (NULL = skip a field).
- * Synchronises the plan's stream. */
+/* Copy rows [first, first + count) of the last run to host arrays (NULL = skip a field). The
+ * copies run on the plan's own stream after the last run and are waited for; work enqueued after
+ * that run on a stream the plan shares keeps running meanwhile. */
 ts_status ts_batch_copy_rows(const ts_batch *b, uint64_t first, uint64_t count, uint32_t *q_idx,
                              uint32_t *e_idx, double *t_in, double *t_out);
 

@@ -387,7 +387,10 @@ ts_status ts_batch_copy_rows(const ts_batch *h, uint64_t first, uint64_t count, 
         set_error("ts_batch_copy_rows: rows beyond the plan's capacity");
         return TS_ERR_INVALID_ARG;
     }
-    cudaStream_t s = p->last_stream ? p->last_stream : p->stream;
+    // on the plan's own stream, after its last run: a stream the plan shares with later work
+    // (plans run one after another) keeps running while the rows are read
+    cudaStream_t s = p->stream;
+    if (p->done) TS_CUDA(cudaStreamWaitEvent(s, p->done, 0));
     if (count) {
         if (q_idx) TS_CUDA(cudaMemcpyAsync(q_idx, p->b.out_q + first, 4 * count, cudaMemcpyDeviceToHost, s));
         if (e_idx) TS_CUDA(cudaMemcpyAsync(e_idx, p->b.out_e + first, 4 * count, cudaMemcpyDeviceToHost, s));

@@ -151,6 +151,7 @@ void destroy_plan(BatchPlan *p)
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     for (int e = 0; e < 4; e++)
         if (p->ev[e]) cudaEventDestroy(p->ev[e]);
+    if (p->done) cudaEventDestroy(p->done);
     p->magic = 0;
     delete p;
 }
@@ -235,6 +236,7 @@ ts_status create_plan(const Index *ix, const ts_batch_params *prm, cudaStream_t 
     TS_CUDA(cudaMemsetAsync(p->dmem, 0, p->dbytes, p->stream));
     TS_CUDA(cudaStreamSynchronize(p->stream));
     for (int e = 0; e < 4; e++) TS_CUDA(cudaEventCreate(&p->ev[e]));
+    TS_CUDA(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
     *out = p.release();
     return TS_OK;
 }
@@ -384,8 +386,8 @@ ts_status plan_run(BatchPlan *p, uint32_t nreq, const ts_segments *qs, const ts_
     } else {
         TS_CHECK(enqueue_run(p, st, p->own_rows));
     }
+    TS_CUDA(cudaEventRecord(p->done, st));
     p->running = true;
-    p->last_stream = st;
     p->last_nreq = nreq;
     return TS_OK;
 }
@@ -412,7 +414,7 @@ ts_status plan_wait(BatchPlan *p, ts_batch_status *out)
         set_error("batch wait: no run in flight");
         return TS_ERR_INVALID_ARG;
     }
-    TS_CUDA(cudaStreamSynchronize(p->last_stream));
+    TS_CUDA(cudaEventSynchronize(p->done));
     p->running = false;
     const uint32_t st = p->h_out->status;
     ts_batch_status bs;

@@ -52,8 +52,10 @@ struct BatchPlan {
     cudaGraphExec_t exec = nullptr;
     unsigned long long graph_kernels = 0;  // kernel launches captured in the graph
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // count pass, write pass bounds
+    // recorded after each run on the stream it ran on: waiting for a run, and copying its rows
+    // on the plan's own stream, need not wait for later work on a stream the plan shares
+    cudaEvent_t done = nullptr;
     bool running = false;
-    cudaStream_t last_stream = nullptr;
     uint32_t last_nreq = 0;
 };
 

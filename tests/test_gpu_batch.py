@@ -114,6 +114,37 @@ def test_plan_runs_equal_plain(use_graph):
     plan.free()
 
 
+def test_plans_sharing_a_stream_are_waited_for_one_by_one():
+    """Plans run one after another on one stream (the end-to-end step's order for large plans):
+    waiting for the first waits for its own run, its rows are read on its own stream while the
+    second plan's run may still be on the shared stream, and every request of both plans equals
+    its plain search."""
+    import torch
+    w = workloads.tiny()
+    rng = np.random.default_rng(21)
+    idx = {k: api.ts_build_index(w.db, kind=k) for k in ("temporal", "spatial")}
+    plans = {k: api.BatchPlan(idx[k], max_requests=8, max_queries=4000, max_rows=400000,
+                              use_graph=True) for k in idx}
+    shared = torch.cuda.Stream()
+    for trial in range(2):
+        reqs = _requests(w, rng, 5)
+        for k in plans:
+            plans[k].run(reqs, stream=shared.cuda_stream)
+        for k in plans:
+            st = plans[k].wait()
+            assert not st["overflow"] and st["nreq"] == len(reqs)
+            rows, spans = plans[k].rows_to_host()
+            assert sum(n for _, n in spans) == st["rows"]
+            for r, req in enumerate(reqs):
+                f, n = spans[r]
+                got = {c: v[f:f + n] for c, v in rows.items()}
+                o = np.lexsort((got["e_idx"], got["q_idx"]))
+                _same({c: v[o] for c, v in got.items()}, _plain(idx[k], req))
+    for k in plans:
+        plans[k].free()
+        idx[k].free()
+
+
 @pytest.mark.parametrize("kind", ["temporal", "spatial"])
 def test_plan_rows_equal_with_and_without_scratch(kind):
     """The count pass keeps its hits for placement after the scan; the tiles with hits that a
