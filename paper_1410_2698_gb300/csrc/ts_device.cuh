@@ -99,8 +99,9 @@ struct Quad {
 // t_lo is the later of the two starts (the query's clipped w0, where its record holds its
 // position, or the entry's t0), so one of the two positions at t_lo is a start point as stored
 // and only the other segment is advanced, by dt = t_lo - its own start: s r0 = (p_adv + v_adv dt)
-// - p_start, where s = +1 when the query is the segment advanced and -1 when the entry is. The
-// sign reaches only b, and is put back with an exclusive-or of b's sign bit (integer pipe).
+// - p_start, where s = +1 when the query is the segment advanced and -1 when the entry is. With
+// dv taken in the same orientation (s dv = v_adv - v_start), b = (s r0).(s dv) needs no sign
+// correction, and a and c do not depend on s.
 static __device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e, Quad &o)
 {
     double t_lo, t_hi;
@@ -123,14 +124,14 @@ static __device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e,
     const double rx = fma(adv_q ? q.vx : e.vx, dt, adv_q ? q.xw : e.x0) - (adv_q ? e.x0 : q.xw);
     const double ry = fma(adv_q ? q.vy : e.vy, dt, adv_q ? q.yw : e.y0) - (adv_q ? e.y0 : q.yw);
     const double rz = fma(adv_q ? q.vz : e.vz, dt, adv_q ? q.zw : e.z0) - (adv_q ? e.z0 : q.zw);
-    const double dvx = q.vx - e.vx, dvy = q.vy - e.vy, dvz = q.vz - e.vz;
+    const double dvx = (adv_q ? q.vx : e.vx) - (adv_q ? e.vx : q.vx);
+    const double dvy = (adv_q ? q.vy : e.vy) - (adv_q ? e.vy : q.vy);
+    const double dvz = (adv_q ? q.vz : e.vz) - (adv_q ? e.vz : q.vz);
     o.t_lo = t_lo;
     o.T = t_hi - t_lo;
     o.a = fma(dvz, dvz, fma(dvy, dvy, dvx * dvx));
-    const double sb = fma(rz, dvz, fma(ry, dvy, rx * dvx));  // s b
-    o.b = __longlong_as_double(__double_as_longlong(sb) ^
-                               (adv_q ? 0ll : (long long)0x8000000000000000ull));
-    o.c = fma(rz, rz, fma(ry, ry, fma(rx, rx, -q.dd)));
+    o.b = fma(rz, dvz, fma(ry, dvy, rx * dvx));
+    o.c = fma(rz, rz, fma(ry, ry, fma(rx, rx, q.ndd)));
     return true;
 }
 
@@ -148,10 +149,11 @@ static __device__ __forceinline__ bool neg(double x)
 static __device__ __forceinline__ bool nonpos(double x) { return dbits(x) <= 0; }
 // x == 0
 static __device__ __forceinline__ bool zero(double x) { return (dbits(x) << 1) == 0; }
-// |x| < |y|: the magnitudes order as their bit patterns without the sign
+// |x| < |y|: the magnitudes order as their bit patterns with the sign bit shifted out (a shift,
+// not a mask: the compiler reads a masked-off sign bit as an FP64 absolute value)
 static __device__ __forceinline__ bool mag_lt(double x, double y)
 {
-    return (dbits(x) & 0x7fffffffffffffffll) < (dbits(y) & 0x7fffffffffffffffll);
+    return ((unsigned long long)dbits(x) << 1) < ((unsigned long long)dbits(y) << 1);
 }
 
 // |x| within [2^-1000, 2^1000) (its biased exponent, sign ignored): the range where the refined
@@ -199,10 +201,12 @@ static __device__ __forceinline__ double sqrt_nr(double x)
 // The interval comes from the numerically stable root pair s/a, c/s (s = -(b + sign(b)
 // sqrt(disc))). The square root and the two quotients come from the refined estimates above
 // (relative error about 2^-40 each, so a few 1e-12 of the roots: far inside the 1e-9 interval
-// tolerance); values outside their range take the library's sqrt and division. The roots need no comparison of their values: with
-// s of the sign opposite to b's sign bit, s/a is the smaller root when b's sign bit is clear and
-// the larger when it is set (c/s is the other), and every clamp compares a value with 0 or two
-// non-negative values, which the integer pipe does on the bit patterns.
+// tolerance); values outside their range take the library's sqrt and division. The code carries
+// t = -s and writes the roots as (-t)/a and (-c)/t, so that the negations are operand modifiers
+// of the multiplies rather than FP64 instructions of their own. The roots need no comparison of
+// their values: with s of the sign opposite to b's sign bit, s/a is the smaller root when b's
+// sign bit is clear and the larger when it is set (c/s is the other), and every clamp compares a
+// value with 0 or two non-negative values, which the integer pipe does on the bit patterns.
 static __device__ __forceinline__ bool quad_solve(const Quad &k, bool interval, double *tin,
                                                   double *tout)
 {
@@ -225,14 +229,14 @@ static __device__ __forceinline__ bool quad_solve(const Quad &k, bool interval, 
     } else {
         if (neg(disc)) disc = 0.0;  // only reachable within rounding of a tangency
         const double sq = nr_range(disc) ? sqrt_nr(disc) : sqrt(disc);
-        const double s = -(k.b + copysign(sq, k.b));
+        const double t = k.b + copysign(sq, k.b);  // -s
         double r1, r2;
-        if (zero(s)) {
+        if (zero(t)) {
             r1 = 0.0;
             r2 = 0.0;
         } else {
-            r1 = nr_range(k.a) ? s * rcp_nr(k.a) : s / k.a;
-            r2 = nr_range(s) ? k.c * rcp_nr(s) : k.c / s;
+            r1 = nr_range(k.a) ? (-t) * rcp_nr(k.a) : (-t) / k.a;
+            r2 = nr_range(t) ? (-k.c) * rcp_nr(t) : (-k.c) / t;
         }
         const bool b_sign = dbits(k.b) < 0;  // sign bit (also for -0.0, as copysign reads it)
         const double lo = b_sign ? r2 : r1, hi = b_sign ? r1 : r2;

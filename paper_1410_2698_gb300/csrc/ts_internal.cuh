@@ -38,11 +38,12 @@ struct __align__(16) SegD {
 static_assert(sizeof(SegD) == 64, "SegD is 64 bytes");
 
 // Exact data of one query segment: its position at the start w0 of its clipped window [w0, w1],
-// its velocity, and the request's d^2.
+// its velocity, and minus the request's d^2 (the addend of c, stored negated so that no FP64
+// instruction negates it).
 struct __align__(16) QueryD {
     double xw, yw, zw, w0;
     double vx, vy, vz, w1;
-    double dd, pad;
+    double ndd, pad;
 };
 static_assert(sizeof(QueryD) == 80, "QueryD is 80 bytes");
 

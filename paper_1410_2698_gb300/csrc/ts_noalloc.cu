@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(NA_WARPS * 32) k_na_tiles(NaParams P)
             M.q.xw = fma(M.q.vx, dw, v[0]);
             M.q.yw = fma(M.q.vy, dw, v[1]);
             M.q.zw = fma(M.q.vz, dw, v[2]);
-            M.q.dd = P.dd;
+            M.q.ndd = -P.dd;
             M.q.pad = 0.0;
             float mn[3], mx[3];
             for (int d = 0; d < 3; d++) {

@@ -226,7 +226,7 @@ __global__ void k_qprep(PrepParams P)
         q.xw = fma(q.vx, dw, v[0]);
         q.yw = fma(q.vy, dw, v[1]);
         q.zw = fma(q.vz, dw, v[2]);
-        q.dd = R.dd;
+        q.ndd = -R.dd;
         q.pad = 0.0;
         const bool valid = fin && (v[7] > v[3]) && (q.w0 < q.w1);
         P.b.qd[i] = q;
