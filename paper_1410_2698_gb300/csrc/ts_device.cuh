@@ -87,6 +87,17 @@ static __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar
 static __device__ __forceinline__ double dmx(double a, double b) { return a > b ? a : b; }
 static __device__ __forceinline__ double dmn(double a, double b) { return a < b ? a : b; }
 
+// The bit pattern of an FP64 value, read through a register move the compiler cannot see into:
+// integer tests on the pattern (signs, zeros, orders, below) then stay integer instructions,
+// where a plain reinterpretation lets the compiler turn some of them back into FP64 compares and
+// absolute values.
+static __device__ __forceinline__ long long dbits(double x)
+{
+    long long v;
+    asm("mov.b64 %0, %1;" : "=l"(v) : "d"(x));
+    return v;
+}
+
 struct Quad {
     double t_lo, T, a, b, c;
 };
@@ -106,8 +117,8 @@ static __device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e,
 {
     double t_lo, t_hi;
     bool adv_q;  // the entry starts at t_lo (or both do): advance the query
-    const long long a0 = __double_as_longlong(q.w0), b0 = __double_as_longlong(e.t0);
-    const long long a1 = __double_as_longlong(q.w1), b1 = __double_as_longlong(e.t1);
+    const long long a0 = dbits(q.w0), b0 = dbits(e.t0);
+    const long long a1 = dbits(q.w1), b1 = dbits(e.t1);
     if ((a0 | b0 | a1 | b1) >= 0) {
         adv_q = b0 >= a0;
         const long long lo = adv_q ? b0 : a0, hi = a1 < b1 ? a1 : b1;
@@ -138,7 +149,6 @@ static __device__ __forceinline__ bool pair_quad(const QueryD &q, const SegD &e,
 // Sign and order tests of FP64 values made on their bit patterns, so that they run on the integer
 // pipe instead of the FP64 pipe (on GB300 an FP64 instruction costs as much pipe time as 32 integer
 // ones). For values that are not NaN; -0.0 and +0.0 compare equal, as in IEEE arithmetic.
-static __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 // x < 0 (sign bit set and not -0.0)
 static __device__ __forceinline__ bool neg(double x)
 {
