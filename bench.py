@@ -41,16 +41,16 @@ INTERVAL_FLOPS = 10  # FP64 flops per hit for the roots (sqrt, 2 div, clamps; sq
 # dram__bytes_write.sum; the gathered FP64 records and the kept hits). The merger-like workload at
 # a tenth of the particles (merger-like-2m) stands in for the full one, whose launches are too
 # large to capture: the per-unit counts are those of the same kernel at the same hit ratio.
-_MERGER_PROFILE = {"fp64_inst_per_exact": 44.15, "warp_inst_per_test": 0.5065,
-                   "dram_bytes_per_exact": 62.51, "hit_ratio": 0.8697,
+_MERGER_PROFILE = {"fp64_inst_per_exact": 33.84, "warp_inst_per_test": 0.4984,
+                   "dram_bytes_per_exact": 62.28, "hit_ratio": 0.8697,
                    "capture": "profiles/k_pair_merger-like-2m_count-pass.md",
-                   "sources": "e5d42994f5d6b975"}
+                   "sources": "a3229a0ecdb4424b"}
 # the Random-walk 1M workload (filter-bound: the issue slots bind); its DRAM bytes are mostly the
 # records the sweep streams, scaled here by the exact tests of the same workload
-_RW1M_PROFILE = {"fp64_inst_per_exact": 9.44, "warp_inst_per_test": 0.5205,
-                 "dram_bytes_per_exact": 439.2, "hit_ratio": 0.348,
+_RW1M_PROFILE = {"fp64_inst_per_exact": 8.81, "warp_inst_per_test": 0.5197,
+                 "dram_bytes_per_exact": 437.2, "hit_ratio": 0.348,
                  "capture": "profiles/k_pair_random-walk-1m_count-pass.md",
-                 "sources": "e5d42994f5d6b975"}
+                 "sources": "a3229a0ecdb4424b"}
 PAIR_PROFILE = {"merger-like-20m": _MERGER_PROFILE, "merger-like-2m": _MERGER_PROFILE,
                 "random-walk-1m": _RW1M_PROFILE}
 PAIR_SOURCES = ("ts_search.cuh", "ts_internal.cuh", "ts_device.cuh")
