@@ -745,6 +745,10 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
     unsigned long long acc_tests = 0, acc_exact = 0, acc_hits = 0;
     uint32_t qn = 0;                            // queued candidates (warp-uniform)
     uint32_t wt_cur = 0xffffffffu, wt_cnt = 0;  // last tile with hits, its hits so far
+    // count pass: the scratch had room after this warp's last reservation (the warp's own view:
+    // reading the shared counter before every batch of exact tests would put a round trip to L2
+    // in front of each)
+    bool room = true;
 
     // Exact test of the oldest nflush queued candidates, one per lane.
     auto flush = [&](uint32_t nflush) {
@@ -770,10 +774,10 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
         double tin = 0.0, tout = 0.0;
         uint32_t eid = 0;
         const uint32_t tile = tw & PK_MAX_TILES;
-        // the count pass computes hit intervals only while the scratch still has room (after
-        // an overflow the write pass sweeps and computes them)
-        const bool interval = PASS == PASS_WRITE ||
-                              (P.scap != 0 && __ldcg(&B.stats[ST_SCRATCH]) <= P.scap);
+        // the count pass computes hit intervals only while the scratch still has room, as far
+        // as this warp has seen (after an overflow the write pass sweeps and computes them; a
+        // hit is kept only when its slot fits, so a stale view costs at most some intervals)
+        const bool interval = PASS == PASS_WRITE || (P.scap != 0 && room);
         if ((uint32_t)lane < nflush) {
             const uint32_t *ids = P.ids[tw >> 29];
             eid = ids ? ids[pos] : pos;
@@ -793,6 +797,7 @@ __global__ void __launch_bounds__(PK_THREADS, PK_MIN_BLOCKS) k_pair(PairParams P
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(&B.stats[ST_SCRATCH], (unsigned long long)__popc(hm));
                 base = __shfl_sync(FULL, base, 0);
+                room = base + (unsigned long long)__popc(hm) < P.scap;
                 const unsigned long long slot = base + __popc(hm & lt_mask);
                 const bool kept = h && slot < P.scap && interval;
                 if (kept) {
