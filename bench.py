@@ -41,16 +41,16 @@ INTERVAL_FLOPS = 10  # FP64 flops per hit for the roots (sqrt, 2 div, clamps; sq
 # dram__bytes_write.sum; the gathered FP64 records and the kept hits). The merger-like workload at
 # a tenth of the particles (merger-like-2m) stands in for the full one, whose launches are too
 # large to capture: the per-unit counts are those of the same kernel at the same hit ratio.
-_MERGER_PROFILE = {"fp64_inst_per_exact": 33.84, "warp_inst_per_test": 0.4984,
-                   "dram_bytes_per_exact": 62.28, "hit_ratio": 0.8697,
+_MERGER_PROFILE = {"fp64_inst_per_exact": 33.84, "warp_inst_per_test": 0.4961,
+                   "dram_bytes_per_exact": 62.02, "hit_ratio": 0.8697,
                    "capture": "profiles/k_pair_merger-like-2m_count-pass.md",
-                   "sources": "a3229a0ecdb4424b"}
+                   "sources": "2cf662d8c6ac49b1"}
 # the Random-walk 1M workload (filter-bound: the issue slots bind); its DRAM bytes are mostly the
 # records the sweep streams, scaled here by the exact tests of the same workload
-_RW1M_PROFILE = {"fp64_inst_per_exact": 8.81, "warp_inst_per_test": 0.5197,
-                 "dram_bytes_per_exact": 437.2, "hit_ratio": 0.348,
+_RW1M_PROFILE = {"fp64_inst_per_exact": 8.80, "warp_inst_per_test": 0.5090,
+                 "dram_bytes_per_exact": 438.6, "hit_ratio": 0.348,
                  "capture": "profiles/k_pair_random-walk-1m_count-pass.md",
-                 "sources": "a3229a0ecdb4424b"}
+                 "sources": "2cf662d8c6ac49b1"}
 PAIR_PROFILE = {"merger-like-20m": _MERGER_PROFILE, "merger-like-2m": _MERGER_PROFILE,
                 "random-walk-1m": _RW1M_PROFILE}
 PAIR_SOURCES = ("ts_search.cuh", "ts_internal.cuh", "ts_device.cuh")
@@ -610,8 +610,8 @@ def run_gpu(args):
         most = max(rows_per_batch.values()) if rows_per_batch else 0
         if serial:
             # the end-to-end step holds the plans together when the device has room for them at
-            # their exact row counts (each on its own stream), so that the rows of one plan are
-            # copied to the host while the next ones compute; else one plan at a time
+            # their exact row counts, runs them one after another on one stream and copies the
+            # rows of one plan to the host while the next ones compute; else one plan at a time
             e2e_plans = {}
             try:
                 for k in kinds:
@@ -621,8 +621,10 @@ def run_gpu(args):
                     pl.free()
                 e2e_plans = None
             if e2e_plans:
-                line["e2e"] = run_e2e(args, api, w, e2e_plans, order, max_rows=most)
-                line["e2e"]["plans"] = "resident together (rows copied while the next plans run)"
+                line["e2e"] = run_e2e(args, api, w, e2e_plans, order, max_rows=most,
+                                      sequential=True)
+                line["e2e"]["plans"] = ("resident together, run one after another on one stream "
+                                        "(each plan's rows copied while the next plans run)")
                 for pl in e2e_plans.values():
                     pl.free()
             else:
@@ -686,16 +688,17 @@ def _pinned_rows(n):
     return views, t
 
 
-def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
+def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0, sequential=False):
     """The batched step through the C ABI with HOST buffers: the query columns live in pinned
     host memory (the plans read them from there) and every result row is read back into pinned
     host memory inside the timed region (wall clock, the stream synchronised on both sides), in
     chunks of at most E2E_CHUNK_ROWS rows through one pinned buffer (the host memory it holds stays
     bounded whatever the step's rows, also with one process per GPU). With make_plan (plans that
     do not fit together) each index's plan is created, timed over the steps and released in
-    turn. Resident plans run each on its own stream, overlapped (run one after another on one
-    stream, the large merger-like plans' copies overlapped the next plan's pair kernel but ran
-    1.6x slower beside it: 3.18 M against 3.78 M query segs/s)."""
+    turn. With `sequential`, resident plans run one after another on one stream (large plans: the
+    first one's rows are ready a third of the way into the step and each plan's rows are read
+    while the next ones compute); else each on its own stream, overlapped, as in the timed
+    step."""
     import torch
     from paper_1410_2698_gb300.workloads import Segments
     qhost = {f: torch.from_numpy(np.ascontiguousarray(getattr(w.queries, f))).pin_memory()
@@ -743,12 +746,14 @@ def run_e2e(args, api, w, plans, kinds, make_plan=None, max_rows=0):
     copy_ms = 0.0
     # a step is seconds long on the largest workloads: at most 5 timed steps after one warm-up
     steps = args.steps if w.db.n <= 5_000_000 else max(1, min(args.steps, 5))
+    seq = torch.cuda.Stream() if sequential else None
     for s in range(steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2d_s = d2h_s = q_s = 0
         for k in kinds:
-            plans[k].run(reqs, stream=0)  # each plan on its own stream, as in the timed step
+            # (stream 0: each plan on its own stream)
+            plans[k].run(reqs, stream=seq.cuda_stream if seq is not None else 0)
         for k in kinds:
             st = plans[k].wait()  # this plan's run only
             q_s += st["stats"]["n_qsegs"]
