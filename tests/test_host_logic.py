@@ -2,6 +2,7 @@
 roofline arithmetic and the gating of its DRAM-traffic figure on the pair kernel's sources."""
 import ctypes
 import os
+import re
 import sys
 
 import numpy as np
@@ -78,6 +79,20 @@ def test_profile_figures_are_keyed_to_the_pair_kernel_sources(tmp_path):
     b = text.index(b"__global__", a)
     (tmp_path / "ts_search.cu").write_bytes(text[:b] + b"/* inside */ " + text[b:])
     assert bench.pair_source_hash(str(tmp_path)) != h
+
+
+def test_every_profile_entry_names_its_committed_capture():
+    """Each per-unit profile the roofline uses points at a summary under profiles/ that records
+    the same pair-kernel sources hash and the same per-unit figures, so the constants and their
+    evidence cannot drift apart."""
+    for name, prof in bench.PAIR_PROFILE.items():
+        path = os.path.join(ROOT, prof["capture"])
+        assert os.path.isfile(path), (name, path)
+        text = open(path).read()
+        assert prof["sources"] in text, (name, prof["sources"])
+        bold = [float(x) for x in re.findall(r"\*\*([0-9]+(?:\.[0-9]+)?)", text)]
+        for key in ("fp64_inst_per_exact", "warp_inst_per_test", "dram_bytes_per_exact"):
+            assert any(abs(x - prof[key]) < 1e-9 for x in bold), (name, key, prof[key], bold)
 
 
 def test_reference_arm_prints_the_contract_line():
